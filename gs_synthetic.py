@@ -1,0 +1,212 @@
+"""Seeded synthetic inputs for the scale-aware Gaussian rasterizer.
+
+This module is shared by the CUDA path (tests, bench) and by the FP64 oracle's
+tests. It only draws random numbers and rounds them to a storage dtype: it holds
+none of the renderer's arithmetic (no reference grid, no footprint, no density).
+
+Workload recipes (GSASR, arXiv 2501.06838):
+  * N = m * H * W Gaussians per LR image (Sec. 3.2, "Gaussian Embedding"), each a
+    jittered offset o around its reference position (mu = p + o, Sec. 3.2,
+    "Gaussian Primary Head");
+  * per Gaussian, drawn in this order from one PCG64 stream: offset x, offset y,
+    log sigma_x, log sigma_y, rho, r, g, b, alpha;
+  * offsets ~ U[-0.5, 0.5] / sqrt(m) (jitter inside the Gaussian's reference
+    cell), sigma ~ log-uniform in LR pixels, rho ~ U(-0.9, 0.9), RGB and alpha
+    ~ U[0, 1];
+  * float64 draws are rounded to float32 (the "FP32 originals"), then to the
+    storage dtype (bf16 / f16) when one is asked for.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+DTYPES = ("f32", "bf16", "f16")
+NORM_DENSITY = 0
+NORM_PEAK = 1
+
+
+def round_f32(x: np.ndarray) -> np.ndarray:
+    return np.asarray(x, dtype=np.float64).astype(np.float32)
+
+
+def round_bf16_bits(x32: np.ndarray) -> np.ndarray:
+    """float32 -> bfloat16 bit patterns (uint16), round to nearest even."""
+    x32 = np.ascontiguousarray(x32, dtype=np.float32)
+    bits = x32.view(np.uint32).astype(np.uint64)
+    lsb = (bits >> 16) & 1
+    rounded = ((bits + 0x7FFF + lsb) >> 16).astype(np.uint16)
+    nan = np.isnan(x32)
+    if nan.any():
+        rounded[nan] = 0x7FC0
+    return rounded
+
+
+def bf16_bits_to_f32(bits: np.ndarray) -> np.ndarray:
+    return (np.asarray(bits, dtype=np.uint32) << 16).view(np.float32)
+
+
+def storage_round(x64: np.ndarray, dtype: str) -> np.ndarray:
+    """Value actually stored for `dtype`, returned exactly widened to float64."""
+    x32 = round_f32(x64)
+    if dtype == "f32":
+        return x32.astype(np.float64)
+    if dtype == "bf16":
+        return bf16_bits_to_f32(round_bf16_bits(x32)).astype(np.float64)
+    if dtype == "f16":
+        return x32.astype(np.float16).astype(np.float64)
+    raise ValueError(f"unknown dtype {dtype}")
+
+
+def storage_array(x64: np.ndarray, dtype: str) -> np.ndarray:
+    """The raw storage array (float32, uint16 bf16 bits, or float16)."""
+    x32 = round_f32(x64)
+    if dtype == "f32":
+        return x32
+    if dtype == "bf16":
+        return round_bf16_bits(x32)
+    if dtype == "f16":
+        return x32.astype(np.float16)
+    raise ValueError(f"unknown dtype {dtype}")
+
+
+@dataclasses.dataclass
+class GaussianSet:
+    """Physical (post-activation) Gaussian parameters of one image.
+
+    Arrays hold the STORED values widened exactly to float64: what the renderer
+    reads. `originals` keeps the float32 originals when `dtype` is reduced.
+    ref_grid_m > 0: `offset` is o and the centre is mu = p(index) + o.
+    ref_grid_m == 0: `offset` holds the absolute centre mu (LR pixels).
+    """
+    offset: np.ndarray  # [N, 2]
+    sigma: np.ndarray   # [N, 2]
+    rho: np.ndarray     # [N]
+    rgb: np.ndarray     # [N, 3]
+    alpha: np.ndarray   # [N]
+    lr_h: int
+    lr_w: int
+    ref_grid_m: int = 1
+    dtype: str = "f32"
+    originals: "GaussianSet | None" = None
+
+    @property
+    def n(self) -> int:
+        return int(self.rho.shape[0])
+
+    def fields(self):
+        return (self.offset, self.sigma, self.rho, self.rgb, self.alpha)
+
+    def storage(self):
+        """Raw storage arrays (what a device copy of the parameters holds)."""
+        return tuple(storage_array(a, self.dtype) for a in self.fields())
+
+    def with_dtype(self, dtype: str) -> "GaussianSet":
+        base = self.originals if self.originals is not None else self
+        vals = [storage_round(a, dtype) for a in base.fields()]
+        return GaussianSet(*vals, lr_h=base.lr_h, lr_w=base.lr_w,
+                           ref_grid_m=base.ref_grid_m, dtype=dtype,
+                           originals=None if dtype == "f32" else base)
+
+    def subset(self, idx) -> "GaussianSet":
+        idx = np.asarray(idx)
+        return GaussianSet(self.offset[idx], self.sigma[idx], self.rho[idx],
+                           self.rgb[idx], self.alpha[idx], self.lr_h, self.lr_w,
+                           0, self.dtype, None)
+
+
+@dataclasses.dataclass
+class View:
+    """Output request: HR image of out_h x out_w sampled at scale s (Eq. 4)."""
+    lr_h: int
+    lr_w: int
+    out_h: int
+    out_w: int
+    scale: float          # a float32 value
+    trunc_k: float = 3.0  # footprint half-width in sigma; <= 0: untruncated
+    norm: int = NORM_DENSITY
+
+    def __post_init__(self):
+        self.scale = float(np.float32(self.scale))
+        self.trunc_k = float(np.float32(self.trunc_k))
+
+
+def out_size(lr: int, scale: float) -> int:
+    """floor(s * lr) with s the float32 scale (the product is exact in f64)."""
+    return int(math.floor(float(np.float32(scale)) * lr))
+
+
+def draw_gaussians(seed: int, lr_h: int, lr_w: int, m: int = 1,
+                   sigma_range=(0.3, 2.0), dtype: str = "f32",
+                   offset_half=0.5) -> GaussianSet:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = m * lr_h * lr_w
+    u = rng.random((n, 9))
+    cell = 1.0 / math.sqrt(m)
+    lo, hi = math.log(sigma_range[0]), math.log(sigma_range[1])
+    offset = (u[:, 0:2] * 2.0 - 1.0) * offset_half * cell
+    sigma = np.exp(lo + u[:, 2:4] * (hi - lo))
+    rho = -0.9 + 1.8 * u[:, 4]
+    rgb = u[:, 5:8].copy()
+    alpha = u[:, 8].copy()
+    f32 = GaussianSet(*(storage_round(a, "f32") for a in (offset, sigma, rho, rgb, alpha)),
+                      lr_h=lr_h, lr_w=lr_w, ref_grid_m=m, dtype="f32")
+    return f32 if dtype == "f32" else f32.with_dtype(dtype)
+
+
+def grad_out(seed: int, out_h: int, out_w: int) -> np.ndarray:
+    """Upstream gradient ~ N(0, 1) per output element, float32 [3, H, W]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.standard_normal((3, out_h, out_w)).astype(np.float32)
+
+
+def sample_indices(seed: int, n: int, k: int) -> np.ndarray:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.sort(rng.choice(n, size=min(k, n), replace=False))
+
+
+# --------------------------------------------------------------------------
+# The five workloads. Each returns (list of GaussianSet, list of View).
+# --------------------------------------------------------------------------
+
+def config1():
+    """Forward-only FP32: LR 48x48, m=1 (N=2,304), x4 -> 192x192, seed 0."""
+    g = draw_gaussians(0, 48, 48, 1, (0.3, 2.0))
+    return [g], [View(48, 48, 192, 192, 4.0)]
+
+
+def config2():
+    """Forward + adjoint FP32: LR 256x256, m=1 (N=65,536), x4 -> 1024x1024."""
+    g = draw_gaussians(0, 256, 256, 1, (0.3, 2.0))
+    return [g], [View(256, 256, 1024, 1024, 4.0)]
+
+
+def config3_sizes(seed: int = 0, n_images: int = 16):
+    """LR sizes (multiples of 4, W in 64..480, H in 64..360) and s ~ U[1.5, 12]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ws = rng.integers(16, 121, size=n_images) * 4
+    hs = rng.integers(16, 91, size=n_images) * 4
+    ss = rng.uniform(1.5, 12.0, size=n_images).astype(np.float32)
+    return [(int(h), int(w), float(s)) for h, w, s in zip(hs, ws, ss)]
+
+
+def config3(n_images: int = 16):
+    """Batched uneven FP32: 16 images, m=1, non-integer scales in [1.5, 12]."""
+    gs, vs = [], []
+    for i, (h, w, s) in enumerate(config3_sizes(0, n_images)):
+        gs.append(draw_gaussians(100 + i, h, w, 1, (0.3, 2.0)))
+        vs.append(View(h, w, out_size(h, s), out_size(w, s), s))
+    return gs, vs
+
+
+def config4(scale: float = 12.0, dtype: str = "bf16"):
+    """Reduced precision: LR 480x270 (W x H), m=4 (N=518,400), sigma in [0.2, 3]."""
+    g = draw_gaussians(0, 270, 480, 4, (0.2, 3.0), dtype=dtype)
+    return [g], [View(270, 480, out_size(270, scale), out_size(480, scale), scale)]
+
+
+def config5_scales(seed: int = 0, batch: int = 16):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return [float(np.float32(s)) for s in rng.uniform(1.0, 4.0, size=batch)]

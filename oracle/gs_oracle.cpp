@@ -1,0 +1,413 @@
+// FP64 CPU oracle for the scale-aware 2D Gaussian rasterizer of GSASR
+// (arXiv 2501.06838). TEST INFRASTRUCTURE ONLY: the tests, the smoke check and
+// the benchmark's CPU-baseline leg use it to check and time the CUDA library.
+// It shares no code, header or table with the CUDA path, and no product code
+// calls it.
+//
+// What it computes (Sec. 3.1):
+//   G_i(x, y)      = alpha_i * c_i * f_i(x, y)                          (Eq. 1)
+//   f_i(x, y)      = Z_i * exp(-q_i / 2),
+//   q_i            = (u^2/sx^2 - 2 rho u v/(sx sy) + v^2/sy^2) / (1 - rho^2),
+//   Z_i            = 1 / (2 pi sx sy sqrt(1 - rho^2))                    (Eq. 2)
+//                    (norm = peak: Z_i = 1, c is then the peak colour)
+//   I_SR(x, y; s)  = sum_i G_i(x / s, y / s),  u = x/s - mu_x, v = y/s - mu_y
+//                                                                        (Eq. 4)
+// with the sum restricted, as in Algorithm 1, to the pixels inside a box window
+// around each Gaussian. The window is the integer pixel rectangle R_i of the
+// box |x/s - mu_x| <= k sx, |y/s - mu_y| <= k sy, whose edges are computed by a
+// fixed sequence of float32 operations (documented at `rect_f32`), so that the
+// GPU and this oracle take the same integer decision. Everything else is FP64.
+//
+// Centres: with a reference grid of m Gaussians per LR pixel, mu = p + o
+// (Sec. 3.2, Gaussian Primary Head), p on an equal-interval sqrt(m) x sqrt(m)
+// sub-grid of each LR pixel (Sec. 3.2, Gaussian Embedding). With m = 0 the
+// offset array holds mu itself.
+//
+// Adjoint: hand-derived derivatives of the loss L = sum g * I with the windows
+// R_i held fixed (the derivative of a moving window edge is not part of it).
+// A templated complex-step path differentiates the same forward independently.
+//
+// Parity: the forward is pinned by closed forms (Poisson-summation sums and
+// moments, constant-colour fields, separable truncated sums) and brute force;
+// the adjoint by complex step, central differences and torch.autograd.
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdint>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+namespace {
+
+struct OView {
+  int32_t lr_h, lr_w, out_h, out_w;
+  float scale;
+  float trunc_k;
+  int32_t norm;       // 0 density (Eq. 2 as printed), 1 peak
+  int32_t ref_grid_m; // 0 absolute centres, else Gaussians per LR pixel
+};
+
+struct Rect { int32_t x0, x1, y0, y1; };  // inclusive; empty when x0 > x1
+
+int isqrt_exact(int m) {
+  for (int r = 1; r * r <= m; ++r) if (r * r == m) return r;
+  return -1;
+}
+
+// Reference position p of Gaussian `gid` on the sub-grid (float32 values):
+// gid = ((i * W + j) * m + b * n + a), p = (j + d_a, i + d_b),
+// d_a = (2a + 1 - n) / (2n) rounded to float32, then j + d_a rounded to float32.
+void ref_pos(int64_t gid, int m, int lr_w, float* px, float* py) {
+  int n = isqrt_exact(m);
+  int64_t cell = gid / m;
+  int sub = (int)(gid % m);
+  int64_t i = cell / lr_w, j = cell % lr_w;
+  int a = sub % n, b = sub / n;
+  volatile float da = (float)((2.0 * a + 1.0 - n) / (2.0 * n));
+  volatile float db = (float)((2.0 * b + 1.0 - n) / (2.0 * n));
+  volatile float fj = (float)j, fi = (float)i;
+  volatile float sx = fj + da;
+  volatile float sy = fi + db;
+  *px = sx; *py = sy;
+}
+
+// One axis of R_i in float32, no contraction (build with -ffp-contract=off):
+//   c = s * mu;  r = (s * k) * sigma;  lo = ceil(c - r);  hi = floor(c + r);
+//   lo clamped below at 0, hi clamped above at n_out - 1.
+void rect_axis_f32(float mu, float sigma, float s, float k, int n_out, int32_t* lo_out, int32_t* hi_out) {
+  volatile float c = s * mu;
+  volatile float sk = s * k;
+  volatile float r = sk * sigma;
+  volatile float a = c - r;
+  volatile float b = c + r;
+  float lo = std::ceil((float)a);
+  float hi = std::floor((float)b);
+  if (!(lo >= 0.0f)) lo = 0.0f;              // also maps NaN to 0
+  if (!(hi <= (float)(n_out - 1))) hi = (float)(n_out - 1);
+  if (lo > (float)(n_out - 1) || hi < 0.0f || lo > hi) { *lo_out = 1; *hi_out = 0; return; }
+  *lo_out = (int32_t)lo; *hi_out = (int32_t)hi;
+}
+
+struct Params {
+  const double *off, *sig, *rho, *rgb, *alpha;
+  int64_t n;
+};
+
+void centre_f32(const Params& P, const OView& V, int64_t i, float* mx, float* my) {
+  float ox = (float)P.off[2 * i], oy = (float)P.off[2 * i + 1];
+  if (V.ref_grid_m > 0) {
+    float px, py;
+    ref_pos(i, V.ref_grid_m, V.lr_w, &px, &py);
+    volatile float sx = px + ox, sy = py + oy;
+    *mx = sx; *my = sy;
+  } else {
+    *mx = ox; *my = oy;
+  }
+}
+
+void centre_f64(const Params& P, const OView& V, int64_t i, double* mx, double* my) {
+  double px = 0.0, py = 0.0;
+  if (V.ref_grid_m > 0) {
+    float fx, fy;
+    ref_pos(i, V.ref_grid_m, V.lr_w, &fx, &fy);
+    px = fx; py = fy;
+  }
+  *mx = px + P.off[2 * i];
+  *my = py + P.off[2 * i + 1];
+}
+
+Rect rect_of(const Params& P, const OView& V, int64_t i) {
+  Rect R;
+  if (!(V.trunc_k > 0.0f)) { R.x0 = 0; R.x1 = V.out_w - 1; R.y0 = 0; R.y1 = V.out_h - 1; return R; }
+  float mx, my;
+  centre_f32(P, V, i, &mx, &my);
+  rect_axis_f32(mx, (float)P.sig[2 * i], V.scale, V.trunc_k, V.out_w, &R.x0, &R.x1);
+  rect_axis_f32(my, (float)P.sig[2 * i + 1], V.scale, V.trunc_k, V.out_h, &R.y0, &R.y1);
+  return R;
+}
+
+// Membership used by the all-pairs mode: the defining inequalities in float32
+// (x >= s*mu - s*k*sigma and x <= s*mu + s*k*sigma), with no integer rectangle.
+bool inside_f32(const Params& P, const OView& V, int64_t i, int x, int y) {
+  if (!(V.trunc_k > 0.0f)) return true;
+  float mx, my;
+  centre_f32(P, V, i, &mx, &my);
+  float s = V.scale, k = V.trunc_k;
+  volatile float cx = s * mx, cy = s * my, sk = s * k;
+  volatile float rx = sk * (float)P.sig[2 * i], ry = sk * (float)P.sig[2 * i + 1];
+  volatile float ax = cx - rx, bx = cx + rx, ay = cy - ry, by = cy + ry;
+  float fx = (float)x, fy = (float)y;
+  return fx >= ax && fx <= bx && fy >= ay && fy <= by;
+}
+
+// The Gaussian's physical parameters as a scalar type T (double or complex).
+template <class T> struct GaussT {
+  T mx, my, sx, sy, rho, c[3], alpha;
+};
+
+template <class T> GaussT<T> gauss_of(const Params& P, const OView& V, int64_t i) {
+  GaussT<T> g;
+  double mx, my;
+  centre_f64(P, V, i, &mx, &my);
+  g.mx = mx; g.my = my;
+  g.sx = P.sig[2 * i]; g.sy = P.sig[2 * i + 1];
+  g.rho = P.rho[i];
+  for (int k = 0; k < 3; ++k) g.c[k] = P.rgb[3 * i + k];
+  g.alpha = P.alpha[i];
+  return g;
+}
+
+// f(x/s, y/s) of Eq. 2 for one Gaussian.
+template <class T> T density(const GaussT<T>& g, double s, int norm, int x, int y) {
+  const double kPi = 3.14159265358979323846;
+  T u = (double)x / s - g.mx;
+  T v = (double)y / s - g.my;
+  T D = (1.0 - g.rho) * (1.0 + g.rho);
+  T q = (u * u / (g.sx * g.sx) - 2.0 * g.rho * u * v / (g.sx * g.sy) + v * v / (g.sy * g.sy)) / D;
+  T Z = norm == 0 ? T(1.0) / (2.0 * kPi * g.sx * g.sy * std::sqrt(D)) : T(1.0);
+  return Z * std::exp(-0.5 * q);
+}
+
+int resolve_threads(int threads) {
+  if (threads > 0) return threads;
+  unsigned h = std::thread::hardware_concurrency();
+  return h ? (int)h : 1;
+}
+
+template <class F> void parallel_for(int64_t n, int threads, F&& fn) {
+  threads = (int)std::min<int64_t>(std::max(1, threads), std::max<int64_t>(1, n));
+  if (threads <= 1) { fn(0, n, 0); return; }
+  std::vector<std::thread> pool;
+  int64_t chunk = (n + threads - 1) / threads;
+  for (int t = 0; t < threads; ++t) {
+    int64_t b = t * chunk, e = std::min(n, b + chunk);
+    if (b >= e) break;
+    pool.emplace_back([&, b, e, t] { fn(b, e, t); });
+  }
+  for (auto& th : pool) th.join();
+}
+
+bool valid_view(const OView* V) {
+  if (!V) return false;
+  if (V->out_h <= 0 || V->out_w <= 0 || V->lr_h <= 0 || V->lr_w <= 0) return false;
+  if (!(V->scale > 0.0f) || !std::isfinite(V->scale)) return false;
+  if (V->ref_grid_m < 0 || (V->ref_grid_m > 0 && isqrt_exact(V->ref_grid_m) < 0)) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Integer rectangles R_i, [n][4] = (x0, x1, y0, y1), inclusive (empty: x0 > x1).
+int gso_rects(const double* off, const double* sig, const double* rho, const double* rgb,
+              const double* alpha, int64_t n, const OView* V, int32_t* rects) {
+  if (!valid_view(V)) return 1;
+  Params P{off, sig, rho, rgb, alpha, n};
+  for (int64_t i = 0; i < n; ++i) {
+    Rect R = rect_of(P, *V, i);
+    rects[4 * i] = R.x0; rects[4 * i + 1] = R.x1; rects[4 * i + 2] = R.y0; rects[4 * i + 3] = R.y1;
+  }
+  return 0;
+}
+
+// Forward render into out[3][out_h][out_w] (overwritten).
+// mode 0: loop each Gaussian over its rectangle (Algorithm 1's loop order),
+//         rows of the output split into bands across threads;
+// mode 1: all pairs: every pixel against every Gaussian, float32 membership test.
+// rects_in (optional, [n][4]) overrides R_i (frozen windows for derivative tests).
+int gso_render(const double* off, const double* sig, const double* rho, const double* rgb,
+               const double* alpha, int64_t n, const OView* V, int mode, int threads,
+               const int32_t* rects_in, double* out) {
+  if (!valid_view(V)) return 1;
+  Params P{off, sig, rho, rgb, alpha, n};
+  const OView v = *V;
+  const int64_t H = v.out_h, W = v.out_w;
+  std::memset(out, 0, sizeof(double) * 3 * H * W);
+  threads = resolve_threads(threads);
+  const double s = (double)v.scale;
+  if (mode == 1) {
+    parallel_for(H, threads, [&](int64_t y0, int64_t y1, int) {
+      for (int64_t y = y0; y < y1; ++y)
+        for (int64_t x = 0; x < W; ++x)
+          for (int64_t i = 0; i < n; ++i) {
+            if (!inside_f32(P, v, i, (int)x, (int)y)) continue;
+            GaussT<double> g = gauss_of<double>(P, v, i);
+            double f = density(g, s, v.norm, (int)x, (int)y);
+            for (int k = 0; k < 3; ++k) out[(k * H + y) * W + x] += g.alpha * g.c[k] * f;
+          }
+    });
+    return 0;
+  }
+  std::vector<Rect> R(n);
+  parallel_for(n, threads, [&](int64_t b, int64_t e, int) {
+    for (int64_t i = b; i < e; ++i) {
+      if (rects_in) R[i] = Rect{rects_in[4 * i], rects_in[4 * i + 1], rects_in[4 * i + 2], rects_in[4 * i + 3]};
+      else R[i] = rect_of(P, v, i);
+    }
+  });
+  parallel_for(H, threads, [&](int64_t yb, int64_t ye, int) {
+    for (int64_t i = 0; i < n; ++i) {
+      const Rect& r = R[i];
+      int64_t ylo = std::max<int64_t>(r.y0, yb), yhi = std::min<int64_t>(r.y1, ye - 1);
+      if (r.x0 > r.x1 || ylo > yhi) continue;
+      GaussT<double> g = gauss_of<double>(P, v, i);
+      for (int64_t y = ylo; y <= yhi; ++y)
+        for (int64_t x = r.x0; x <= r.x1; ++x) {
+          double f = density(g, s, v.norm, (int)x, (int)y);
+          for (int k = 0; k < 3; ++k) out[(k * H + y) * W + x] += g.alpha * g.c[k] * f;
+        }
+    }
+  });
+  return 0;
+}
+
+// Hand adjoint of L = sum_{k,y,x} grad_out[k,y,x] * I[k,y,x] with frozen R_i.
+// grads[n][9] = dL/d(o_x, o_y, sigma_x, sigma_y, rho, r, g, b, alpha).
+//   per pixel: G = sum_k g_k c_k, f = Z exp(-q/2)
+//   dc_k += g_k alpha f;  dalpha += G f;
+//   dtheta += G alpha f (dlogZ/dtheta - dq/dtheta / 2)
+//   dq/dmu_x = -(2u/sx^2 - 2 rho v/(sx sy)) / D
+//   dq/dmu_y = -(2v/sy^2 - 2 rho u/(sx sy)) / D
+//   dq/dsx   = -(2u^2/sx^3 - 2 rho u v/(sx^2 sy)) / D
+//   dq/dsy   = -(2v^2/sy^3 - 2 rho u v/(sx sy^2)) / D
+//   dq/drho  = (-2uv/(sx sy) + 2 rho q) / D
+//   density: dlogZ/dsx = -1/sx, dlogZ/dsy = -1/sy, dlogZ/drho = rho/D; peak: 0.
+//   mu = p + o, so dL/do = dL/dmu.
+int gso_adjoint(const double* off, const double* sig, const double* rho, const double* rgb,
+                const double* alpha, int64_t n, const OView* V, const double* grad_out,
+                int threads, const int32_t* rects_in, double* grads) {
+  if (!valid_view(V)) return 1;
+  Params P{off, sig, rho, rgb, alpha, n};
+  const OView v = *V;
+  const int64_t H = v.out_h, W = v.out_w;
+  const double s = (double)v.scale;
+  const double kPi = 3.14159265358979323846;
+  threads = resolve_threads(threads);
+  parallel_for(n, threads, [&](int64_t b, int64_t e, int) {
+    for (int64_t i = b; i < e; ++i) {
+      Rect r = rects_in ? Rect{rects_in[4 * i], rects_in[4 * i + 1], rects_in[4 * i + 2], rects_in[4 * i + 3]}
+                        : rect_of(P, v, i);
+      double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+      GaussT<double> g = gauss_of<double>(P, v, i);
+      const double sx = g.sx, sy = g.sy, rh = g.rho;
+      const double D = (1.0 - rh) * (1.0 + rh);
+      const double Z = v.norm == 0 ? 1.0 / (2.0 * kPi * sx * sy * std::sqrt(D)) : 1.0;
+      const double dlz_sx = v.norm == 0 ? -1.0 / sx : 0.0;
+      const double dlz_sy = v.norm == 0 ? -1.0 / sy : 0.0;
+      const double dlz_rh = v.norm == 0 ? rh / D : 0.0;
+      if (r.x0 <= r.x1 && r.y0 <= r.y1) {
+        for (int64_t y = r.y0; y <= r.y1; ++y)
+          for (int64_t x = r.x0; x <= r.x1; ++x) {
+            const double u = (double)x / s - g.mx, w = (double)y / s - g.my;
+            const double q = (u * u / (sx * sx) - 2.0 * rh * u * w / (sx * sy) + w * w / (sy * sy)) / D;
+            const double f = Z * std::exp(-0.5 * q);
+            double gk[3], G = 0.0;
+            for (int k = 0; k < 3; ++k) { gk[k] = grad_out[(k * H + y) * W + x]; G += gk[k] * g.c[k]; }
+            const double dq_mx = -(2.0 * u / (sx * sx) - 2.0 * rh * w / (sx * sy)) / D;
+            const double dq_my = -(2.0 * w / (sy * sy) - 2.0 * rh * u / (sx * sy)) / D;
+            const double dq_sx = -(2.0 * u * u / (sx * sx * sx) - 2.0 * rh * u * w / (sx * sx * sy)) / D;
+            const double dq_sy = -(2.0 * w * w / (sy * sy * sy) - 2.0 * rh * u * w / (sx * sy * sy)) / D;
+            const double dq_rh = (-2.0 * u * w / (sx * sy) + 2.0 * rh * q) / D;
+            const double Gaf = G * g.alpha * f;
+            acc[0] += Gaf * (-0.5 * dq_mx);
+            acc[1] += Gaf * (-0.5 * dq_my);
+            acc[2] += Gaf * (dlz_sx - 0.5 * dq_sx);
+            acc[3] += Gaf * (dlz_sy - 0.5 * dq_sy);
+            acc[4] += Gaf * (dlz_rh - 0.5 * dq_rh);
+            for (int k = 0; k < 3; ++k) acc[5 + k] += gk[k] * g.alpha * f;
+            acc[8] += G * f;
+          }
+      }
+      for (int k = 0; k < 9; ++k) grads[9 * i + k] = acc[k];
+    }
+  });
+  return 0;
+}
+
+// Complex-step derivatives of the same loss for the Gaussians listed in gids:
+// dL/dtheta = Im(L(theta + i h)) / h, evaluated with the forward's own formula
+// (templated on std::complex<double>) and the frozen windows. grads[k][9].
+int gso_complex_step(const double* off, const double* sig, const double* rho, const double* rgb,
+                     const double* alpha, int64_t n, const OView* V, const double* grad_out,
+                     const int64_t* gids, int64_t k, double h, double* grads) {
+  if (!valid_view(V)) return 1;
+  Params P{off, sig, rho, rgb, alpha, n};
+  const OView v = *V;
+  const int64_t H = v.out_h, W = v.out_w;
+  const double s = (double)v.scale;
+  typedef std::complex<double> C;
+  for (int64_t t = 0; t < k; ++t) {
+    const int64_t i = gids[t];
+    if (i < 0 || i >= n) return 2;
+    Rect r = rect_of(P, v, i);
+    GaussT<double> g0 = gauss_of<double>(P, v, i);
+    for (int p = 0; p < 9; ++p) {
+      GaussT<C> g;
+      g.mx = g0.mx; g.my = g0.my; g.sx = g0.sx; g.sy = g0.sy; g.rho = g0.rho;
+      for (int c = 0; c < 3; ++c) g.c[c] = g0.c[c];
+      g.alpha = g0.alpha;
+      const C ih(0.0, h);
+      switch (p) {
+        case 0: g.mx += ih; break;
+        case 1: g.my += ih; break;
+        case 2: g.sx += ih; break;
+        case 3: g.sy += ih; break;
+        case 4: g.rho += ih; break;
+        case 5: g.c[0] += ih; break;
+        case 6: g.c[1] += ih; break;
+        case 7: g.c[2] += ih; break;
+        default: g.alpha += ih; break;
+      }
+      C L(0.0, 0.0);
+      if (r.x0 <= r.x1 && r.y0 <= r.y1)
+        for (int64_t y = r.y0; y <= r.y1; ++y)
+          for (int64_t x = r.x0; x <= r.x1; ++x) {
+            C f = density(g, s, v.norm, (int)x, (int)y);
+            for (int c = 0; c < 3; ++c) L += grad_out[(c * H + y) * W + x] * (g.alpha * g.c[c] * f);
+          }
+      grads[9 * t + p] = L.imag() / h;
+    }
+  }
+  return 0;
+}
+
+// One Gaussian's share of the loss, L_i = sum_{(x,y) in R_i} g(x,y) . G_i(x/s, y/s),
+// with its 9 parameters replaced by theta = (mu_x, mu_y, sigma_x, sigma_y, rho,
+// r, g, b, alpha) and R_i computed from the UNPERTURBED inputs (frozen window).
+// Central differences of this function check the adjoint.
+double gso_gaussian_loss(const double* off, const double* sig, const double* rho, const double* rgb,
+                         const double* alpha, int64_t n, const OView* V, const double* grad_out,
+                         int64_t gid, const double* theta) {
+  if (!valid_view(V) || gid < 0 || gid >= n) return NAN;
+  Params P{off, sig, rho, rgb, alpha, n};
+  const OView v = *V;
+  const int64_t H = v.out_h, W = v.out_w;
+  Rect r = rect_of(P, v, gid);
+  GaussT<double> g;
+  g.mx = theta[0]; g.my = theta[1]; g.sx = theta[2]; g.sy = theta[3]; g.rho = theta[4];
+  for (int c = 0; c < 3; ++c) g.c[c] = theta[5 + c];
+  g.alpha = theta[8];
+  double L = 0.0;
+  if (r.x0 <= r.x1 && r.y0 <= r.y1)
+    for (int64_t y = r.y0; y <= r.y1; ++y)
+      for (int64_t x = r.x0; x <= r.x1; ++x) {
+        double f = density(g, (double)v.scale, v.norm, (int)x, (int)y);
+        for (int c = 0; c < 3; ++c) L += grad_out[(c * H + y) * W + x] * (g.alpha * g.c[c] * f);
+      }
+  return L;
+}
+
+// The FP64 centre mu = p + o of Gaussian gid (p from the reference grid).
+int gso_centre(const double* off, int64_t n, const OView* V, int64_t gid, double* mu) {
+  if (!valid_view(V) || gid < 0 || gid >= n) return 1;
+  Params P{off, nullptr, nullptr, nullptr, nullptr, n};
+  centre_f64(P, *V, gid, &mu[0], &mu[1]);
+  return 0;
+}
+
+int gso_hardware_threads(void) { return resolve_threads(0); }
+
+}  // extern "C"
