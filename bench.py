@@ -1,0 +1,479 @@
+"""Benchmark of the scale-aware Gaussian rasterizer (GSASR, arXiv 2501.06838).
+
+A step is one pass of the whole hot path over one batch of synthetic input:
+footprint pass, prefix sum, pair emission, radix sort, tile ranges, tile
+raster (forward), and, for workloads with an adjoint, the raster adjoint and
+the parameter chain rule. Default workload: LR 256x256, one Gaussian per LR
+pixel (N = 65,536), x4 -> 1024x1024, forward + adjoint, FP32 parameters.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...     the FP64 CPU oracle on the same workload
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on
+the launching stream; L2 is flushed (256 MiB write) before every step, outside
+the events. Under torchrun every rank renders its own copy of the workload
+(weak scaling, no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import gs_synthetic as S  # noqa: E402
+
+METRIC = "HR Mpix/s fwd and fwd+bwd at ×4/×12 vs FP64 oracle error; % FP32/SFU peak"
+UNIT = "HR Mpix/s"
+
+# ALU roofline of the raster kernels (derivation in the design doc): every FP32 and
+# MUFU instruction takes one issue slot; an SM issues 4 warp-instructions per
+# clock = 128 lane-instructions. The irreducible per-pair work is
+#   forward: 1 FFMA (exponent, row terms hoisted) + 1 MUFU.EX2 + 3 FFMA (RGB)  = 5
+#   adjoint: forward's 2 + 3 (colour grads) + 3 (g.c) + 1 (G w) + 3 (Y moments) = 12
+# MUFU.EX2 issues at 32 lanes/clk/SM on GB300 (probe), so issue binds first.
+SMS = 152
+ISSUE_PER_SM_CLK = 128
+PAIR_COST = {"raster_fwd": 5, "raster_bwd": 12}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# --------------------------------------------------------------------------
+# Workloads
+# --------------------------------------------------------------------------
+WORKLOADS = {
+    "c2": "LR 256x256, m=1 (N=65,536), x4 -> 1024x1024, forward + adjoint, FP32 params",
+    "c1": "LR 48x48, m=1 (N=2,304), x4 -> 192x192, forward, FP32 params",
+    "c4x8-bf16": "LR 480x270, m=4 (N=518,400), x8 -> 3840x2160, forward + adjoint, BF16 params",
+    "c4x12-bf16": "LR 480x270, m=4 (N=518,400), x12 -> 5760x3240, forward + adjoint, BF16 params",
+    "c4x12-f16": "LR 480x270, m=4 (N=518,400), x12 -> 5760x3240, forward + adjoint, FP16 params",
+    "c4x12-f32": "LR 480x270, m=4 (N=518,400), x12 -> 5760x3240, forward + adjoint, FP32 params",
+    "c3": "16 images, LR 64..480 x 64..360, m=1, s ~ U[1.5, 12], batched forward, FP32 params",
+}
+
+
+def workload(name):
+    """-> (list of GaussianSet, list of View, with_adjoint, dtype name)."""
+    if name == "c2":
+        g, v = S.config2()
+        return g, v, True, "f32"
+    if name == "c1":
+        g, v = S.config1()
+        return g, v, False, "f32"
+    if name.startswith("c4x"):
+        sc, dt = name[3:].split("-")
+        g, v = S.config4(float(sc), dt)
+        return g, v, True, dt
+    if name == "c3":
+        g, v = S.config3()
+        return g, v, False, "f32"
+    raise SystemExit(f"unknown workload {name}")
+
+
+# --------------------------------------------------------------------------
+# Clock sampling during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(s[1]) for s in self.samples if num(s[1])]
+        mx = [num(s[2]) for s in self.samples if num(s[2])]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for s in self.samples for n, v in zip(names, s[5:9]) if "Active" in v
+                          and "Not" not in v})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+# --------------------------------------------------------------------------
+# The GPU arm
+# --------------------------------------------------------------------------
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2501_06838_gb300 as gs
+    from paper_2501_06838_gb300 import build as libbuild
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    gsets, views, with_adj, dtname = workload(args.workload)
+    tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[dtname]
+
+    def dev_g(g):
+        arrs = g.storage()
+        ts = []
+        for a in arrs:
+            t = torch.from_numpy(np.ascontiguousarray(a).view(np.int16)).view(torch.bfloat16) \
+                if dtname == "bf16" else torch.from_numpy(np.ascontiguousarray(a))
+            ts.append(t.to(dev).contiguous())
+        return gs.Gaussians(*ts, ref_grid_m=g.ref_grid_m)
+
+    dgs = [dev_g(g) for g in gsets]
+    plan = gs.Plan(dgs, views, tile=args.tile, batch=args.batch, with_grads=with_adj)
+    if with_adj:
+        for i, v in enumerate(views):
+            plan.grad_outs[i].copy_(torch.from_numpy(S.grad_out(1, v.out_h, v.out_w)))
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    hr_pix = sum(v.out_h * v.out_w for v in views)
+
+    def step():
+        plan.fwd(stream)
+        if with_adj:
+            plan.bwd(stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    plan.status()
+    stats = plan.stats()
+    gs.timing_read()
+
+    # ---- timed region (device-resident inputs) ----
+    timed_kernels = ["raster_fwd", "raster_bwd"] if with_adj else ["raster_fwd"]
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    fwd_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = gs.launch_count()
+    gs.timing_enable(timed_kernels)
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        fwd_ev[k][0].record(stream)
+        plan.fwd(stream)
+        fwd_ev[k][1].record(stream)
+        if with_adj:
+            plan.bwd(stream)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    launches = gs.launch_count() - launches0
+    gs.timing_enable([])
+    ktimes = gs.timing_read()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    fwd_ms = [a.elapsed_time(b) for a, b in fwd_ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    plan.status()
+
+    # ---- roofline of the dominant kernel ----
+    peaks, peak_src = load_peaks()
+    f_clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    dom = max(ktimes.items(), key=lambda kv: kv[1][0])[0] if ktimes else None
+    roof = None
+    if dom:
+        ms, cnt = ktimes[dom]
+        per_launch_s = ms / cnt * 1e-3
+        pairs = stats["pixel_pairs"]
+        achieved = pairs / per_launch_s / 1e9
+        peak = SMS * f_clk * ISSUE_PER_SM_CLK / PAIR_COST[dom] / 1e9
+        roof = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 2),
+                "peak": round(peak, 2), "unit": "Gpair/s", "frac": round(achieved / peak, 4),
+                "traffic": None,
+                "peak_basis": (f"{SMS} SMs x {ISSUE_PER_SM_CLK} issue/clk x {f_clk / 1e6:.0f} MHz "
+                               f"/ {PAIR_COST[dom]} instr per pair ({peak_src} sm_max_mhz)"),
+                "pairs_per_launch": pairs, "ms_per_launch": round(ms / cnt, 5)}
+
+    res = {
+        "metric": METRIC, "value": round(world * hr_pix * args.steps / (total_ms * 1e-3) / 1e6, 2),
+        "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(total_ms / args.steps, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": dtname, "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}",
+                   "l2": "flushed before every step (256 MiB write, outside the timed events)",
+                   "tile": plan.V[0].tile or 16, "smem_batch": plan.V[0].batch or 64,
+                   "hr_pixels_per_step": hr_pix, "gaussians": sum(g.n for g in dgs),
+                   "parallelism": f"replicas x{world} (one full workload per GPU)"},
+        "fwd_mpix_s": round(hr_pix * args.steps / (sum(fwd_ms) * 1e-3) / 1e6, 2),
+        "kernel_ms": {k: round(v[0] / v[1], 5) for k, v in ktimes.items()},
+        "pairs": {"pixel_pairs": stats["pixel_pairs"], "tile_pairs": stats["tile_pairs"]},
+        "roofline": roof, "gpu_launches": int(launches), "clocks": clk,
+    }
+
+    # ---- end to end through the public API with host buffers ----
+    if not args.no_e2e:
+        e2e = run_e2e(args, plan, gsets, views, with_adj, dtname, dev, stream, flush)
+        tot = e2e.pop("total_ms")
+        if world > 1:
+            t = torch.tensor([tot], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tot = float(t.item())
+        e2e["value"] = round(world * hr_pix * args.steps / (tot * 1e-3) / 1e6, 2)
+        e2e["ms_per_step"] = round(tot / args.steps, 5)
+        res["e2e"] = e2e
+
+    # ---- CPU baseline: the FP64 oracle on the host cores, bounded sample ----
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cb, err = run_cpu_baseline(gsets, views, with_adj, plan, args.cpu_seconds)
+        res["cpu_baseline"] = cb
+        if err:
+            res["error_vs_oracle"] = err
+    return res
+
+
+def run_e2e(args, plan, gsets, views, with_adj, dtname, dev, stream, flush):
+    """Same metric through Plan.fwd/bwd, with every step copying its inputs from
+    pinned host memory and its results back (copies inside the timed region)."""
+    import torch
+    host_in, dev_in = [], []
+    for g, dg in zip(gsets, plan.gs):
+        for t in dg.tensors():
+            h = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+            h.copy_(t.cpu())
+            host_in.append(h)
+            dev_in.append(t)
+    if with_adj:
+        for go in plan.grad_outs:
+            h = torch.empty(go.shape, dtype=go.dtype, pin_memory=True)
+            h.copy_(go.cpu())
+            host_in.append(h)
+            dev_in.append(go)
+    host_out = [torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in plan.outs]
+    dev_out = list(plan.outs)
+    if with_adj:
+        host_out += [torch.empty(g.shape, dtype=g.dtype, pin_memory=True) for g in plan.grads]
+        dev_out += list(plan.grads)
+    h2d = sum(t.numel() * t.element_size() for t in host_in)
+    d2h = sum(t.numel() * t.element_size() for t in host_out)
+
+    def step():
+        for h, d in zip(host_in, dev_in):
+            d.copy_(h, non_blocking=True)
+        plan.fwd(stream)
+        if with_adj:
+            plan.bwd(stream)
+        for d, h in zip(dev_out, host_out):
+            h.copy_(d, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    tot = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        b.synchronize()
+        tot += a.elapsed_time(b)
+    return {"unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "total_ms": tot}
+
+
+def oracle_step(gsets, views, with_adj, band=None, threads=0, grad_outs=None):
+    """One oracle step: render (and adjoint) of every image, or of the top
+    `band` rows of every image. Returns (images, grads, HR pixels done)."""
+    import oracle
+    outs, grads, px = [], [], 0
+    for i, (g, v) in enumerate(zip(gsets, views)):
+        vv = v if band is None else S.View(v.lr_h, v.lr_w, min(band, v.out_h), v.out_w, v.scale,
+                                           v.trunc_k, v.norm)
+        outs.append(oracle.render(g, vv, threads=threads))
+        if with_adj:
+            go = grad_outs[i] if grad_outs is not None else S.grad_out(1, v.out_h, v.out_w)
+            grads.append(oracle.adjoint(g, vv, go[:, :vv.out_h], threads=threads))
+        px += vv.out_h * vv.out_w
+    return outs, grads, px
+
+
+def sample_band(gsets, views, with_adj, budget):
+    """None if one oracle step of the whole workload fits in `budget` seconds,
+    else the number of top rows per image that does (probed on 256 rows)."""
+    probe = min(256, max(v.out_h for v in views))
+    t0 = time.time()
+    oracle_step(gsets, views, with_adj, band=probe)
+    t = time.time() - t0
+    full = t * max(v.out_h for v in views) / probe
+    if full <= budget:
+        return None
+    return max(16, int(probe * budget / max(t, 1e-9)))
+
+
+def run_cpu_baseline(gsets, views, with_adj, plan, seconds):
+    """Times the FP64 oracle (fwd + adjoint when the workload has one) on all
+    host cores, on a bounded sample: whole images when a step fits in a few
+    seconds, else the top rows of each image. Also returns this run's GPU error
+    against it (normwise per channel / per field)."""
+    import oracle
+    oracle.build()
+    cores = oracle.hardware_threads()
+    use_band = sample_band(gsets, views, with_adj, seconds / 2)
+    reps, px, t = 0, 0, 0.0
+    outs = grads = None
+    while t < seconds or reps == 0:
+        t1 = time.time()
+        outs, grads, npx = oracle_step(gsets, views, with_adj, band=use_band)
+        t += time.time() - t1
+        px += npx
+        reps += 1
+        if use_band is None and reps >= 1 and t > seconds / 2:
+            break
+    sample = (f"{reps} oracle step(s) of the full workload" if use_band is None else
+              f"{reps} oracle step(s) on the top {use_band} rows of every image")
+    cb = {"value": round(px / t / 1e6, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+          "sample": sample + (" (fwd + adjoint)" if with_adj else " (fwd)"),
+          "seconds": round(t, 2)}
+    # error of this run's GPU result against the oracle (on the same sample)
+    err = {}
+    try:
+        img_err = []
+        for o, ref in zip(plan.outs, outs):
+            a = o[:, :ref.shape[1]].cpu().double().numpy()
+            img_err.append(float((np.abs(a - ref).max(axis=(1, 2)) / np.abs(ref).max(axis=(1, 2))).max()))
+        err["image_normwise"] = max(img_err)
+        if with_adj and use_band is None:
+            ge = []
+            for gr, ref in zip(plan.grads, grads):
+                a = gr.cpu().double().numpy()
+                ge.append(float((np.abs(a - ref).max(axis=0) / np.abs(ref).max(axis=0)).max()))
+            err["grad_normwise"] = max(ge)
+    except Exception as e:  # keep the bench line even if the comparison fails
+        err["error"] = repr(e)
+    return cb, err
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle itself, timed per step on the host."""
+    if rank != 0:
+        return None
+    import oracle
+    oracle.build()
+    gsets, views, with_adj, dtname = workload(args.workload)
+    band = sample_band(gsets, views, with_adj, max(1.0, args.ref_step_seconds))
+    for _ in range(args.warmup):
+        oracle_step(gsets, views, with_adj, band=band)
+    tot, px = 0.0, 0
+    for _ in range(args.steps):
+        t1 = time.time()
+        _, _, npx = oracle_step(gsets, views, with_adj, band=band)
+        tot += time.time() - t1
+        px += npx
+    val = round(px / tot / 1e6, 4)
+    sample = ("the full workload per step" if band is None else
+              f"the top {band} rows of every image per step")
+    cores = oracle.hardware_threads()
+    return {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(tot / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample + (" (fwd + adjoint)" if with_adj else " (fwd)")},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-step-seconds", type=float, default=3.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+        if res is not None:
+            print(json.dumps(res), flush=True)
+        return
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    import __graft_entry__
+    __graft_entry__.build()
+    res = run_gpu(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,188 @@
+/*
+ * gs.h -- C-ABI of the GB300 (sm_103a) scale-aware 2D Gaussian rasterizer.
+ *
+ * The library renders N image Gaussians into a super-resolved image at any
+ * scale factor s and back-propagates through the render, as defined by GSASR
+ * (arXiv 2501.06838):
+ *   Sec. 3.1, Eq. 1   G(x, y) = alpha * c * f(x, y)
+ *   Sec. 3.1, Eq. 2   f = (2 pi sx sy sqrt(1 - rho^2))^-1
+ *                         * exp(-(dx^2/sx^2 - 2 rho dx dy/(sx sy) + dy^2/sy^2)
+ *                                / (2 (1 - rho^2)))
+ *   Sec. 3.1, Eq. 4   I_SR(x, y; s) = sum_i G_i(x / s, y / s)
+ *   Algorithm 1       each Gaussian only touches the HR pixels of a box window
+ *                     around its centre; here the box is the footprint
+ *                     |x/s - mu_x| <= k sx, |y/s - mu_y| <= k sy (k = trunc_k),
+ *                     taken as an integer pixel rectangle whose edges are the
+ *                     float32 values ceil(s mu - (s k) sigma), floor(s mu + (s k) sigma)
+ *                     (round to nearest, no fused multiply-add), clamped to the
+ *                     image.
+ *   Sec. 3.1, "Fast Rasterization", and Sec. 3.2, "Rendering": the render is
+ *                     differentiable; gs_render_bwd gives the gradient of
+ *                     L = sum grad_out * I with the windows held fixed.
+ *   Sec. 3.2, Gaussian Primary Head / Gaussian Embedding: with ref_grid_m = m
+ *                     > 0 the centre is mu = p + o, p on an equal-interval
+ *                     sqrt(m) x sqrt(m) sub-grid of each LR pixel (index order
+ *                     ((i * lr_w + j) * m + b * sqrt(m) + a), p = (j + d_a, i + d_b),
+ *                     d_a = (2a + 1 - sqrt(m)) / (2 sqrt(m)) in float32).
+ *
+ * Coordinates: LR pixel (j, i) is centred at (j, i) (Eq. 3); HR pixel (x, y),
+ * integers in [0, out_w) x [0, out_h), samples the LR point (x/s, y/s) (Eq. 4).
+ * Images are planar float32 [3][out_h][out_w], row-major.
+ *
+ * Conventions for every entry point:
+ *  - Every pointer inside gs_gaussians and every image / gradient pointer is a
+ *    DEVICE pointer (current CUDA device) unless stated otherwise; the caller
+ *    owns all memory. The library allocates no device memory: scratch lives in
+ *    a caller-allocated workspace sized by gs_workspace_size.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    All calls except gs_count_pairs, gs_sync_status and gs_read_stats are
+ *    asynchronous on that stream and may be captured in a CUDA graph.
+ *  - Return value: GS_OK, or a status detected on the host before anything was
+ *    launched (invalid argument, too-small workspace, CUDA launch error); the
+ *    message is available from gs_last_error() (thread-local). Problems found
+ *    on the device while the kernels run (an invalid Gaussian parameter, a pair
+ *    count above the workspace's capacity) are written to a status word in the
+ *    workspace and returned by the next gs_sync_status / gs_read_stats.
+ *  - Gradients are overwritten, never accumulated.
+ *  - No call waits on another kernel through a spin loop; nothing here traps.
+ */
+#ifndef GS_H
+#define GS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GS_OK = 0,
+  GS_ERR_INVALID = 1,      /* bad argument, or (device) a non-finite / out-of-range parameter */
+  GS_ERR_CAPACITY = 2,     /* (device) more (tile, Gaussian) pairs than the workspace holds */
+  GS_ERR_CUDA = 3,         /* a CUDA runtime call or launch failed */
+  GS_ERR_UNSUPPORTED = 4,  /* a valid request this build does not implement */
+  GS_ERR_TIMEOUT = 5,      /* reserved: a bounded device-side wait gave up */
+  GS_ERR_INTERNAL = 6      /* an internal consistency check failed */
+} gs_status;
+
+typedef enum { GS_F32 = 0, GS_BF16 = 1, GS_F16 = 2 } gs_dtype;
+
+typedef enum {
+  GS_NORM_DENSITY = 0,  /* Eq. 2 as printed: Z = 1 / (2 pi sx sy sqrt(1 - rho^2)) */
+  GS_NORM_PEAK = 1      /* Z = 1: c is the colour at the centre (the "peak RGB" reading) */
+} gs_norm;
+
+/* Physical (post-activation) parameters of n Gaussians, structure of arrays,
+ * contiguous, all of element type `dtype`. Device pointers, caller-owned. */
+typedef struct gs_gaussians {
+  const void* offset; /* [n][2] o (ref_grid_m > 0) or absolute mu (ref_grid_m == 0), LR px */
+  const void* sigma;  /* [n][2] (sigma_x, sigma_y) > 0, LR px */
+  const void* rho;    /* [n]    correlation, |rho| < 1 */
+  const void* rgb;    /* [n][3] colour c */
+  const void* alpha;  /* [n]    opacity */
+  int64_t n;          /* number of Gaussians; must equal m * lr_h * lr_w when ref_grid_m > 0 */
+  int32_t dtype;      /* gs_dtype of all five arrays */
+  int32_t ref_grid_m; /* 0, 1, 4, 9 or 16 */
+} gs_gaussians;
+
+/* One output request. tile and batch are launch parameters (0 = defaults);
+ * every view of one batched call must use the same tile. */
+typedef struct gs_view {
+  int32_t lr_h, lr_w;   /* LR grid (used by the reference grid and for validation) */
+  int32_t out_h, out_w; /* HR output size, 1 <= out <= floor(s * lr) + 1 */
+  float scale;          /* s > 0 */
+  float trunc_k;        /* footprint half-width in sigma (3.0); <= 0: whole image */
+  int32_t norm;         /* gs_norm */
+  int32_t tile;         /* screen tile edge in HR px: 8, 16 or 32 (0 = 16) */
+  int32_t batch;        /* Gaussians per shared-memory batch, 32..512 (0 = default) */
+  int32_t reserved;     /* must be 0 */
+} gs_view;
+
+/* Counters of the last forward call on a workspace. */
+typedef struct gs_stats {
+  int64_t tile_pairs;   /* P: (tile, Gaussian) pairs emitted for binning */
+  int64_t pixel_pairs;  /* sum_i |R_i|: (Gaussian, HR pixel) pairs inside the windows */
+  int64_t capacity;     /* pair capacity of the workspace */
+  int64_t n_gaussians;  /* total Gaussians over all images */
+  int32_t n_tiles;      /* screen tiles over all images */
+  int32_t status;       /* device status word (gs_status) */
+} gs_stats;
+
+/* Bytes of workspace for rendering n_images images (arrays of n_images entries,
+ * host memory) with room for `pair_capacity` (tile, Gaussian) pairs. Returns 0
+ * when the arguments are invalid (see gs_last_error). Host-only, no CUDA call. */
+size_t gs_workspace_size(int32_t n_images, const gs_gaussians* g, const gs_view* v,
+                         int64_t pair_capacity);
+
+/* Exact number of (tile, Gaussian) pairs the render of these images emits.
+ * Runs the per-Gaussian footprint pass and the prefix sum on `stream` inside
+ * `ws` (which needs capacity >= 0 only), then SYNCHRONISES the stream and
+ * writes the count to *pairs_out (host pointer). Device status problems are
+ * returned directly. */
+gs_status gs_count_pairs(int32_t n_images, const gs_gaussians* g, const gs_view* v,
+                         void* ws, size_t ws_bytes, void* stream, int64_t* pairs_out);
+
+/* Forward render of one image (Eq. 4 with the Algorithm-1 window) into `out`
+ * (device, float32 [3][out_h][out_w], fully overwritten). `ws` (device,
+ * ws_bytes >= gs_workspace_size(1, g, v, cap)) keeps the binned state that
+ * gs_render_bwd needs; do not modify it in between. */
+gs_status gs_render_fwd(const gs_gaussians* g, const gs_view* v, float* out, void* ws,
+                        size_t ws_bytes, void* stream);
+
+/* Adjoint of the last gs_render_fwd on `ws` (same g and v, unchanged values).
+ * grad_out: device float32 [3][out_h][out_w], dL/dI. grads: device float32
+ * [n][9] = dL/d(o_x, o_y, sigma_x, sigma_y, rho, r, g, b, alpha), overwritten
+ * (dL/do = dL/dmu). The windows R_i are held fixed (Eq. 4's sum over a fixed
+ * set of pixels per Gaussian). */
+gs_status gs_render_bwd(const gs_gaussians* g, const gs_view* v, const float* grad_out,
+                        float* grads, void* ws, size_t ws_bytes, void* stream);
+
+/* The forward of n_images independent images (own Gaussians, sizes and scale
+ * each; g, v and outs are host arrays of n_images entries) in one chain of
+ * launches over a global tile index space: one kernel per stage, whatever the
+ * number of images. */
+gs_status gs_render_batched(int32_t n_images, const gs_gaussians* g, const gs_view* v,
+                            float* const* outs, void* ws, size_t ws_bytes, void* stream);
+
+/* Adjoint of the last gs_render_batched on `ws`. grad_outs, grads: host arrays
+ * of device pointers as in gs_render_bwd, one per image. */
+gs_status gs_render_batched_bwd(int32_t n_images, const gs_gaussians* g, const gs_view* v,
+                                const float* const* grad_outs, float* const* grads, void* ws,
+                                size_t ws_bytes, void* stream);
+
+/* Synchronises `stream`, returns the workspace's device status word and resets
+ * it to GS_OK. */
+gs_status gs_sync_status(void* ws, void* stream);
+
+/* Synchronises `stream` and copies the counters of the last forward on `ws`
+ * into *out (host). Does not reset the status. */
+gs_status gs_read_stats(void* ws, void* stream, gs_stats* out);
+
+/* Thread-local text of the last host-side error ("" when none). */
+const char* gs_last_error(void);
+
+/* Static name of a status code. */
+const char* gs_status_string(int32_t status);
+
+/* Number of kernels this library has launched in this process. */
+int64_t gs_launch_count(void);
+
+/* Per-kernel timing with CUDA events recorded around each launch on the
+ * launching stream (off by default; not for use under stream capture).
+ * kernel_mask: bit k times kernel id k (see gs_kernel_name); 0 turns timing
+ * off, -1 times every kernel. gs_timing_read synchronises the recorded events,
+ * adds each kernel's time since the last read into ms_out[k] and its launches
+ * into count_out[k] for k < n, returns the number of kernel ids, and clears the
+ * record. */
+gs_status gs_timing_enable(int32_t kernel_mask);
+int32_t gs_timing_read(double* ms_out, int64_t* count_out, int32_t n);
+const char* gs_kernel_name(int32_t id);
+
+/* Library build identity, e.g. "gs 0.1 sm_103a". */
+const char* gs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS_H */

@@ -1,0 +1,193 @@
+// Internal definitions shared by the CUDA translation units of libgs.
+// Not part of the public ABI (include/gs.h).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gs {
+
+// Status bits of the device status word (mapped to gs_status on the host).
+enum : uint32_t { kStInvalid = 1u, kStCapacity = 2u, kStInternal = 4u, kStTimeout = 8u };
+
+constexpr int kSetupChunk = 16;       // image descriptors per setup launch
+constexpr int kFootprintBlock = 256;  // Gaussians per footprint / emit block
+constexpr int kRecordF4 = 4;          // a record is 4 float4 = 64 B
+
+// Per-image descriptor, copied into the workspace at the start of each call.
+struct ImageDesc {
+  const void* off;
+  const void* sig;
+  const void* rho;
+  const void* rgb;
+  const void* alpha;
+  float* out;
+  const float* grad_out;
+  float* grads;
+  int64_t n;
+  int64_t g_base;   // first global Gaussian index of this image
+  int32_t dtype, m, lr_h, lr_w, out_h, out_w;
+  float scale, trunc_k;
+  int32_t norm, tiles_x, tiles_y, t_base;  // t_base: first global tile index
+};
+static_assert(sizeof(ImageDesc) == 128, "ImageDesc layout");
+
+struct SetupChunk {
+  int32_t first, count, reset, pad;
+  ImageDesc d[kSetupChunk];
+};
+
+// Workspace header (device).
+struct Header {
+  uint32_t status;
+  uint32_t pad0;
+  unsigned long long pairs;        // P, total (tile, Gaussian) pairs
+  unsigned long long pixel_pairs;  // sum_i |R_i|
+  unsigned long long capacity;
+  uint32_t work_counter;
+  uint32_t pad1;
+  unsigned long long reserved[11];
+};
+static_assert(sizeof(Header) == 128, "Header layout");
+
+// Per-Gaussian record written by the footprint pass (64 B):
+//   f0 = (cx_hi, cx_lo, cy_hi, cy_lo)  HR-pixel centre s*mu as exact float pairs
+//   f1 = (sA, sK, g, l)                exponent, log2 units, X = x - cx, Y = y - cy (HR px):
+//                                      e = -(sA X - sK Y)^2 + g Y^2 + l
+//                                        = A X^2 + B X Y + C Y^2 + l  (Eq. 2's quadratic
+//                                      form completed in X: sA = sqrt(-A), sK = B/(2 sA),
+//                                      g = C - B^2/(4A), the Y-marginal)
+//   f2 = (alpha r, alpha g, alpha b, 0)
+//   f3 = (x0, x1, y0, y1)              integer window R_i, inclusive (x0 > x1: empty)
+// Tile rectangle of the same Gaussian (16 B, emit pass):
+//   (first key, tiles_x of its image, tiles wide, tiles high); count = w * h.
+
+// Device pointers into the caller's workspace, plus sizes.
+struct Ws {
+  Header* hdr;
+  ImageDesc* images;
+  float4* records;            // [N][4]
+  uint4* trect;               // [N]
+  uint32_t* counts;           // [N]
+  unsigned long long* parts;  // per-footprint-block pair counts, scanned in place
+  uint32_t* keys[2];          // [capacity]
+  uint32_t* vals[2];          // [capacity]
+  uint32_t* hist;             // [256][sort_blocks], row-scanned in place
+  uint32_t* hscan;            // [256] per-digit totals
+  uint2* ranges;              // [T]
+  float* grec;                // [N][12] record-space gradient moments
+  int64_t n;                  // total Gaussians
+  int64_t capacity;           // pair capacity
+  int32_t n_images;
+  int32_t tiles;              // total tiles
+  int32_t tile;               // tile edge (8, 16, 32)
+  int32_t tile_shift;
+  int32_t sort_blocks;
+  int32_t scan_parts;         // size of `parts`
+};
+
+// ---------------------------------------------------------------------------
+// Small device helpers.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float ex2_approx(float x) {
+  // MUFU.EX2 (2^x on the special-function unit), flush-to-zero; ex2(-inf) = +0.
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float load_param(const void* p, int64_t i, int dtype) {
+  if (dtype == 0) return __ldg(reinterpret_cast<const float*>(p) + i);
+  if (dtype == 1) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(p)[i]);
+  return __half2float(reinterpret_cast<const __half*>(p)[i]);
+}
+
+// Highest image index whose first Gaussian index is <= gi.
+__device__ __forceinline__ int image_of_gaussian(const ImageDesc* im, int n_images, int64_t gi) {
+  int lo = 0, hi = n_images - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (im[mid].g_base <= gi) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int image_of_tile(const ImageDesc* im, int n_images, int t) {
+  int lo = 0, hi = n_images - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (im[mid].t_base <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <class T>
+__device__ __forceinline__ T warp_inclusive_scan(T v) {
+  const int lane = threadIdx.x & 31;
+  for (int o = 1; o < 32; o <<= 1) {
+    T u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
+  }
+  return v;
+}
+
+// Exclusive block scan; returns the exclusive prefix of v and the block total.
+template <class T, int NT>
+__device__ __forceinline__ T block_exclusive_scan(T v, T* smem_warp, T& total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T incl = warp_inclusive_scan(v);
+  if (lane == 31) smem_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    T x = lane < NT / 32 ? smem_warp[lane] : T(0);
+    T xi = warp_inclusive_scan(x);
+    if (lane < NT / 32) smem_warp[lane] = xi - x;
+    if (lane == NT / 32 - 1) smem_warp[NT / 32] = xi;
+  }
+  __syncthreads();
+  T r = smem_warp[warp] + incl - v;
+  total = smem_warp[NT / 32];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ unsigned long long effective_pairs(const Header* h) {
+  unsigned long long p = h->pairs;
+  return p <= h->capacity ? p : 0ull;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (one per translation unit), all asynchronous on stream.
+// Each returns the cudaError_t of its launches.
+// ---------------------------------------------------------------------------
+cudaError_t launch_setup(const SetupChunk& c, const Ws& w, cudaStream_t s);
+cudaError_t launch_preprocess(const Ws& w, cudaStream_t s);
+cudaError_t launch_preprocess_bwd(const Ws& w, cudaStream_t s);
+cudaError_t launch_scan_counts(const Ws& w, cudaStream_t s);
+cudaError_t launch_emit(const Ws& w, cudaStream_t s);
+cudaError_t launch_sort(const Ws& w, int passes, cudaStream_t s, int* final_buf);
+cudaError_t launch_ranges(const Ws& w, const uint32_t* sorted_keys, cudaStream_t s);
+cudaError_t launch_raster_fwd(const Ws& w, const uint32_t* sorted_vals, int batch, cudaStream_t s);
+cudaError_t launch_raster_bwd(const Ws& w, const uint32_t* sorted_vals, int batch, cudaStream_t s);
+
+// Kernel ids for launch accounting / per-kernel timing.
+enum KernelId {
+  kKSetup = 0, kKPreprocess, kKReserved2, kKScanTop, kKRadixRowscan, kKEmit, kKRadixHist,
+  kKRadixScatter, kKRanges, kKRasterFwd, kKRasterBwd, kKPreprocessBwd, kKMemset, kKNumKernels
+};
+
+// Launch bookkeeping implemented in gs_api.cu: every launch goes through
+// begin/end so that the launch counter and the optional event timing see it.
+void launch_begin(int kernel_id, cudaStream_t s);
+void launch_end(int kernel_id, cudaStream_t s);
+
+struct LaunchScope {
+  int id;
+  cudaStream_t s;
+  LaunchScope(int id_, cudaStream_t s_) : id(id_), s(s_) { launch_begin(id, s); }
+  ~LaunchScope() { launch_end(id, s); }
+};
+
+}  // namespace gs

@@ -1,0 +1,249 @@
+// Per-Gaussian passes of the scale-aware rasterizer (GSASR, arXiv 2501.06838):
+//   k_setup           copies the image table into the workspace, resets counters
+//   k_preprocess      footprint pass: parameters -> record, window R_i, tile count
+//   k_preprocess_bwd  record-space gradient moments -> parameter gradients
+#include "gs_internal.cuh"
+
+namespace gs {
+
+namespace {
+
+constexpr float kLog2E = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+constexpr float kLog2TwoPi = 2.6514961294723187f;
+
+__global__ void k_setup(SetupChunk c, Ws w) {
+  int t = threadIdx.x;
+  if (t < c.count) w.images[c.first + t] = c.d[t];
+  if (c.reset && t == 0) {
+    Header* h = w.hdr;
+    h->status = 0u;
+    h->pairs = 0ull;
+    h->pixel_pairs = 0ull;
+    h->capacity = (unsigned long long)w.capacity;
+    h->work_counter = 0u;
+    h->reserved[0] = (unsigned long long)w.n;
+    h->reserved[1] = (unsigned long long)w.tiles;
+  }
+}
+
+// Integer window edge on one axis, in float32 with round-to-nearest and no
+// contraction (the __f*_rn intrinsics are never fused):
+//   c = s * mu, r = (s * k) * sigma, lo = ceil(c - r), hi = floor(c + r),
+//   lo clamped to >= 0, hi to <= n_out - 1; empty -> lo = 1, hi = 0.
+__device__ __forceinline__ void window_axis(float mu, float sig, float s, float k, int n_out,
+                                            int& lo, int& hi) {
+  float c = __fmul_rn(s, mu);
+  float sk = __fmul_rn(s, k);
+  float r = __fmul_rn(sk, sig);
+  float flo = ceilf(__fsub_rn(c, r));
+  float fhi = floorf(__fadd_rn(c, r));
+  float last = (float)(n_out - 1);
+  if (!(flo >= 0.0f)) flo = 0.0f;
+  if (!(fhi <= last)) fhi = last;
+  if (flo > last || fhi < 0.0f || flo > fhi) { lo = 1; hi = 0; return; }
+  lo = (int)flo;
+  hi = (int)fhi;
+}
+
+__device__ __forceinline__ int grid_root(int m) { return m == 1 ? 1 : m == 4 ? 2 : m == 9 ? 3 : 4; }
+
+__global__ void __launch_bounds__(kFootprintBlock) k_preprocess(Ws w) {
+  __shared__ unsigned long long sw[kFootprintBlock / 32 + 1];
+  // Clear the tile ranges (grid-stride) so empty tiles read (0, 0).
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < w.tiles;
+       t += (int64_t)gridDim.x * blockDim.x)
+    w.ranges[t] = make_uint2(0u, 0u);
+
+  const int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  unsigned long long pix = 0ull;
+  uint32_t cnt = 0u;
+  if (gi < w.n) {
+    const int im = image_of_gaussian(w.images, w.n_images, gi);
+    const ImageDesc& D = w.images[im];
+    const int64_t li = gi - D.g_base;
+    const int dt = D.dtype;
+    const float ox = load_param(D.off, 2 * li, dt), oy = load_param(D.off, 2 * li + 1, dt);
+    const float sx = load_param(D.sig, 2 * li, dt), sy = load_param(D.sig, 2 * li + 1, dt);
+    const float rho = load_param(D.rho, li, dt);
+    const float cr = load_param(D.rgb, 3 * li, dt), cg = load_param(D.rgb, 3 * li + 1, dt),
+                cb = load_param(D.rgb, 3 * li + 2, dt);
+    const float al = load_param(D.alpha, li, dt);
+    const bool ok = isfinite(ox) && isfinite(oy) && isfinite(cr) && isfinite(cg) && isfinite(cb) &&
+                    isfinite(al) && sx > 0.0f && sy > 0.0f && isfinite(sx) && isfinite(sy) &&
+                    rho > -1.0f && rho < 1.0f;
+    const float s = D.scale;
+
+    // Reference position p (float32) and the two centres: mu32 = fl(p + o) for
+    // the window, and s * (p + o) as an exact float pair (hi + lo) for the
+    // exponent (TwoSum of p + o, then TwoProduct of s times its head).
+    float px = 0.0f, py = 0.0f;
+    if (D.m > 0) {
+      const int n = grid_root(D.m);
+      const int64_t cell = li / D.m;
+      const int sub = (int)(li - cell * D.m);
+      const int64_t i = cell / D.lr_w, j = cell - i * D.lr_w;
+      const int a = sub % n, b = sub / n;
+      const float da = __fdiv_rn((float)(2 * a + 1 - n), (float)(2 * n));
+      const float db = __fdiv_rn((float)(2 * b + 1 - n), (float)(2 * n));
+      px = __fadd_rn((float)j, da);
+      py = __fadd_rn((float)i, db);
+    }
+    float mux, muy, ex, ey;
+    if (D.m > 0) {
+      mux = __fadd_rn(px, ox);
+      float bb = __fsub_rn(mux, px);
+      ex = __fadd_rn(__fsub_rn(px, __fsub_rn(mux, bb)), __fsub_rn(ox, bb));
+      muy = __fadd_rn(py, oy);
+      bb = __fsub_rn(muy, py);
+      ey = __fadd_rn(__fsub_rn(py, __fsub_rn(muy, bb)), __fsub_rn(oy, bb));
+    } else {
+      mux = ox; muy = oy; ex = 0.0f; ey = 0.0f;
+    }
+    const float cx_hi = __fmul_rn(s, mux);
+    const float cx_lo = __fadd_rn(__fmaf_rn(s, mux, -cx_hi), __fmul_rn(s, ex));
+    const float cy_hi = __fmul_rn(s, muy);
+    const float cy_lo = __fadd_rn(__fmaf_rn(s, muy, -cy_hi), __fmul_rn(s, ey));
+
+    int x0 = 1, x1 = 0, y0 = 1, y1 = 0;
+    if (ok) {
+      if (D.trunc_k > 0.0f) {
+        window_axis(mux, sx, s, D.trunc_k, D.out_w, x0, x1);
+        window_axis(muy, sy, s, D.trunc_k, D.out_h, y0, y1);
+      } else {
+        x0 = 0; x1 = D.out_w - 1; y0 = 0; y1 = D.out_h - 1;
+      }
+    }
+
+    // Exponent in HR pixels and log2 units: -q/2 of Eq. 2 times log2(e), with
+    // u = X/s, v = Y/s, written with the square completed in X so that no
+    // cancellation occurs however close |rho| is to 1:
+    //   e = -(sA X - sK Y)^2 + g Y^2 + l,
+    //   sA = r / (s sx), sK = rho r / (s sy), r = sqrt(log2(e) / (2 D)),
+    //   g = -log2(e) / (2 s^2 sy^2)   (the Y marginal),  D = (1 - rho)(1 + rho).
+    const float Dr = __fmul_rn(__fsub_rn(1.0f, rho), __fadd_rn(1.0f, rho));
+    const float isx = __frcp_rn(__fmul_rn(s, sx)), isy = __frcp_rn(__fmul_rn(s, sy));
+    const float r = sqrtf(__fdiv_rn(0.5f * kLog2E, Dr));
+    const float sA = r * isx;
+    const float sK = rho * r * isy;
+    const float gY = -0.5f * kLog2E * isy * isy;
+    // Eq. 2 normalisation 1 / (2 pi sx sy sqrt(D)), or 1 for the peak reading.
+    const float l = D.norm == 0 ? -(kLog2TwoPi + log2f(sx) + log2f(sy) + 0.5f * log2f(Dr)) : 0.0f;
+
+    float4* rec = w.records + gi * kRecordF4;
+    rec[0] = make_float4(cx_hi, cx_lo, cy_hi, cy_lo);
+    rec[1] = make_float4(sA, sK, gY, l);
+    rec[2] = make_float4(al * cr, al * cg, al * cb, 0.0f);
+    rec[3] = make_float4(__int_as_float(x0), __int_as_float(x1), __int_as_float(y0), __int_as_float(y1));
+
+    uint4 tr = make_uint4(0u, 0u, 0u, 0u);
+    if (x0 <= x1 && y0 <= y1) {
+      const int tx0 = x0 >> w.tile_shift, tx1 = x1 >> w.tile_shift;
+      const int ty0 = y0 >> w.tile_shift, ty1 = y1 >> w.tile_shift;
+      const uint32_t tw = (uint32_t)(tx1 - tx0 + 1), th = (uint32_t)(ty1 - ty0 + 1);
+      cnt = tw * th;
+      tr = make_uint4((uint32_t)(D.t_base + ty0 * D.tiles_x + tx0), (uint32_t)D.tiles_x, tw, th);
+      pix = (unsigned long long)(x1 - x0 + 1) * (unsigned long long)(y1 - y0 + 1);
+    }
+    w.trect[gi] = tr;
+    w.counts[gi] = cnt;
+    if (!ok) atomicOr(&w.hdr->status, kStInvalid);
+  }
+  // warp sum of the window areas, one atomic per warp
+  for (int o = 16; o > 0; o >>= 1) pix += __shfl_xor_sync(0xffffffffu, pix, o);
+  if ((threadIdx.x & 31) == 0 && pix) atomicAdd(&w.hdr->pixel_pairs, pix);
+  // this block's pair count, scanned over blocks by k_scan_top
+  unsigned long long tot;
+  block_exclusive_scan<unsigned long long, kFootprintBlock>(cnt, sw, tot);
+  if (threadIdx.x == 0 && blockIdx.x < w.scan_parts) w.parts[blockIdx.x] = tot;
+}
+
+// Chain rule from the record space to the parameters. The raster adjoint left,
+// per Gaussian, the moments of Gw = (sum_k g_k c_k) 2^e over its window
+//   m = (S0, SX, SY, SXX, SXY, SYY, Cr, Cg, Cb),
+//   S_ab = sum Gw X^a Y^b, C_k = sum g_k 2^e.
+// With out_k += c_k 2^e and e = A X^2 + B X Y + C Y^2 + l (the record's
+// completed-square form expands to this):
+//   dL/dl = ln2 S0, dL/dA = ln2 SXX, dL/dB = ln2 SXY, dL/dC = ln2 SYY,
+//   dL/dcx = -ln2 (2A SX + B SY), dL/dcy = -ln2 (B SX + 2C SY),
+// and cx = s mu_x, A = -L2/(2 s^2 sx^2 D), B = L2 rho/(s^2 sx sy D),
+// C = -L2/(2 s^2 sy^2 D), l = -log2(2 pi sx sy sqrt D) (density) or 0 (peak),
+// colour record = alpha c (L2 = log2 e, so ln2 * L2 = 1).
+__global__ void __launch_bounds__(256) k_preprocess_bwd(Ws w) {
+  const int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gi >= w.n) return;
+  const int im = image_of_gaussian(w.images, w.n_images, gi);
+  const ImageDesc& D = w.images[im];
+  const int64_t li = gi - D.g_base;
+  float* out = D.grads + li * 9;
+  const float4* rec = w.records + gi * kRecordF4;
+  const float4 r3 = rec[3];
+  const bool live = __float_as_int(r3.x) <= __float_as_int(r3.y) &&
+                    __float_as_int(r3.z) <= __float_as_int(r3.w);
+  if (!live) {
+    for (int k = 0; k < 9; ++k) out[k] = 0.0f;
+    return;
+  }
+  const int dt = D.dtype;
+  const float sx = load_param(D.sig, 2 * li, dt), sy = load_param(D.sig, 2 * li + 1, dt);
+  const float rho = load_param(D.rho, li, dt);
+  const float cr = load_param(D.rgb, 3 * li, dt), cg = load_param(D.rgb, 3 * li + 1, dt),
+              cb = load_param(D.rgb, 3 * li + 2, dt);
+  const float al = load_param(D.alpha, li, dt);
+  const float s = D.scale;
+  const float Dr = __fmul_rn(__fsub_rn(1.0f, rho), __fadd_rn(1.0f, rho));
+  const float isx = __frcp_rn(__fmul_rn(s, sx)), isy = __frcp_rn(__fmul_rn(s, sy));
+  const float q = __fdiv_rn(kLog2E, Dr);
+  const float A = -0.5f * q * isx * isx;
+  const float B = q * rho * isx * isy;
+  const float C = -0.5f * q * isy * isy;
+  const float* m = w.grec + gi * 12;
+  const float S0 = m[0], SX = m[1], SY = m[2], SXX = m[3], SXY = m[4], SYY = m[5];
+  const float Cr = m[6], Cg = m[7], Cb = m[8];
+
+  const float dcx = -kLn2 * (2.0f * A * SX + B * SY);
+  const float dcy = -kLn2 * (B * SX + 2.0f * C * SY);
+  const float dens = D.norm == 0 ? 1.0f : 0.0f;
+  const float dsx = (kLn2 * (-2.0f * A * SXX - B * SXY) - dens * S0) / sx;
+  const float dsy = (kLn2 * (-2.0f * C * SYY - B * SXY) - dens * S0) / sy;
+  const float two_r_over_D = 2.0f * rho / Dr;
+  const float drho = kLn2 * two_r_over_D * (A * SXX + C * SYY) +
+                     SXY * (1.0f + rho * rho) / (s * s * sx * sy * Dr * Dr) +
+                     dens * S0 * rho / Dr;
+  out[0] = s * dcx;
+  out[1] = s * dcy;
+  out[2] = dsx;
+  out[3] = dsy;
+  out[4] = drho;
+  out[5] = al * Cr;
+  out[6] = al * Cg;
+  out[7] = al * Cb;
+  out[8] = cr * Cr + cg * Cg + cb * Cb;
+}
+
+}  // namespace
+
+cudaError_t launch_setup(const SetupChunk& c, const Ws& w, cudaStream_t s) {
+  LaunchScope ls(kKSetup, s);
+  k_setup<<<1, 32, 0, s>>>(c, w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_preprocess(const Ws& w, cudaStream_t s) {
+  int64_t work = w.n > (int64_t)w.tiles ? w.n : (int64_t)w.tiles;
+  int blocks = (int)((work + kFootprintBlock - 1) / kFootprintBlock);
+  if (blocks < 1) blocks = 1;
+  LaunchScope ls(kKPreprocess, s);
+  k_preprocess<<<blocks, kFootprintBlock, 0, s>>>(w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_preprocess_bwd(const Ws& w, cudaStream_t s) {
+  if (w.n == 0) return cudaSuccess;
+  int blocks = (int)((w.n + 255) / 256);
+  LaunchScope ls(kKPreprocessBwd, s);
+  k_preprocess_bwd<<<blocks, 256, 0, s>>>(w);
+  return cudaGetLastError();
+}
+
+}  // namespace gs

@@ -1,0 +1,335 @@
+"""PyTorch-facing binding of the GSASR scale-aware rasterizer (libgs.so).
+
+PyTorch provides device memory and streams; all arithmetic of the render and
+its adjoint runs in the library's CUDA kernels (include/gs.h). Functions:
+
+  count_pairs(gs, views)                    exact (tile, Gaussian) pair count (syncs)
+  render(g, view) / render_batched(gs, views)          forward (Eq. 4, Algorithm 1)
+  render_bwd(...) / render_batched_bwd(...)            adjoint with frozen windows
+  GSRender.apply(offset, sigma, rho, rgb, alpha, view)  autograd, one image
+  GSRenderBatched.apply(views, m, sizes, offset, ...)   autograd, uneven batch
+
+Parameters are physical (post-activation): offset o (or absolute centre when
+ref_grid_m == 0), sigma, rho, rgb, alpha, all in LR pixels (GSASR, arXiv
+2501.06838, Sec. 3.1-3.2), stored as float32, bfloat16 or float16.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+from typing import Sequence
+
+import torch
+
+from . import _abi
+
+_DTYPES = {torch.float32: _abi.GS_F32, torch.bfloat16: _abi.GS_BF16, torch.float16: _abi.GS_F16}
+
+
+@dataclasses.dataclass
+class Gaussians:
+    """Device parameters of one image's Gaussians (contiguous tensors)."""
+    offset: torch.Tensor  # [N, 2]
+    sigma: torch.Tensor   # [N, 2]
+    rho: torch.Tensor     # [N]
+    rgb: torch.Tensor     # [N, 3]
+    alpha: torch.Tensor   # [N]
+    ref_grid_m: int = 1
+
+    @property
+    def n(self) -> int:
+        return int(self.rho.shape[0])
+
+    def tensors(self):
+        return (self.offset, self.sigma, self.rho, self.rgb, self.alpha)
+
+    @staticmethod
+    def from_arrays(arrays, ref_grid_m: int, device="cuda", dtype=torch.float32):
+        """From host arrays (numpy or tensors) of (offset, sigma, rho, rgb, alpha)."""
+        ts = [torch.as_tensor(a).to(device=device, dtype=dtype).contiguous() for a in arrays]
+        return Gaussians(*ts, ref_grid_m=ref_grid_m)
+
+
+def _struct_g(g: Gaussians) -> _abi.GsGaussians:
+    ts = g.tensors()
+    dt = ts[0].dtype
+    if dt not in _DTYPES:
+        raise TypeError(f"unsupported parameter dtype {dt}")
+    n = g.n
+    shapes = ((n, 2), (n, 2), (n,), (n, 3), (n,))
+    for t, shp in zip(ts, shapes):
+        if t.dtype != dt:
+            raise TypeError("all parameter tensors must share one dtype")
+        if not t.is_cuda:
+            raise ValueError("parameter tensors must be CUDA tensors")
+        if not t.is_contiguous() or tuple(t.shape) != shp:
+            raise ValueError(f"parameter tensor must be contiguous with shape {shp}, got {tuple(t.shape)}")
+    return _abi.GsGaussians(ts[0].data_ptr(), ts[1].data_ptr(), ts[2].data_ptr(),
+                            ts[3].data_ptr(), ts[4].data_ptr(), n, _DTYPES[dt], int(g.ref_grid_m))
+
+
+def _struct_v(v, tile: int = 0, batch: int = 0) -> _abi.GsView:
+    tile = tile or getattr(v, "tile", 0) or 0
+    batch = batch or getattr(v, "batch", 0) or 0
+    return _abi.GsView(int(v.lr_h), int(v.lr_w), int(v.out_h), int(v.out_w), float(v.scale),
+                       float(getattr(v, "trunc_k", 3.0)), int(getattr(v, "norm", 0)),
+                       int(tile), int(batch), 0)
+
+
+def _arrays(gs: Sequence[Gaussians], views, tile=0, batch=0):
+    n = len(gs)
+    if n != len(views) or n == 0:
+        raise ValueError("need one view per image and at least one image")
+    G = (_abi.GsGaussians * n)(*[_struct_g(g) for g in gs])
+    V = (_abi.GsView * n)(*[_struct_v(v, tile, batch) for v in views])
+    return n, G, V
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+class Workspace:
+    """Caller-owned device scratch for one render (and its adjoint)."""
+
+    def __init__(self, nbytes: int, device=None):
+        self.buf = torch.empty(int(nbytes), dtype=torch.uint8, device=device or "cuda")
+        if self.buf.data_ptr() % 256:
+            raise RuntimeError("workspace allocation is not 256-byte aligned")
+
+    @property
+    def ptr(self) -> int:
+        return self.buf.data_ptr()
+
+    @property
+    def nbytes(self) -> int:
+        return self.buf.numel()
+
+
+def workspace_bytes(gs, views, capacity: int, tile=0, batch=0) -> int:
+    n, G, V = _arrays(gs, views, tile, batch)
+    b = _abi.load().gs_workspace_size(n, G, V, int(capacity))
+    if b == 0:
+        raise _abi.GsError(_abi.GS_ERR_INVALID, "gs_workspace_size", _abi.last_error())
+    return int(b)
+
+
+def count_pairs(gs, views, tile=0, batch=0, stream=None) -> int:
+    """Exact number of (tile, Gaussian) pairs; synchronises the stream."""
+    n, G, V = _arrays(gs, views, tile, batch)
+    dev = gs[0].rho.device
+    ws = Workspace(workspace_bytes(gs, views, 0, tile, batch), dev)
+    out = ctypes.c_int64(0)
+    _abi.check(_abi.load().gs_count_pairs(n, G, V, ws.ptr, ws.nbytes, _stream(stream),
+                                          ctypes.byref(out)), "gs_count_pairs")
+    return int(out.value)
+
+
+def make_workspace(gs, views, capacity=None, tile=0, batch=0, slack: float = 0.0,
+                   stream=None) -> Workspace:
+    if capacity is None:
+        capacity = count_pairs(gs, views, tile, batch, stream)
+    capacity = int(capacity * (1.0 + slack)) + (1 if slack else 0)
+    return Workspace(workspace_bytes(gs, views, capacity, tile, batch), gs[0].rho.device)
+
+
+def render_batched(gs, views, outs=None, ws: Workspace | None = None, tile=0, batch=0,
+                   stream=None, check: bool = False):
+    """Forward render of several images in one launch chain. Returns (outs, ws)."""
+    n, G, V = _arrays(gs, views, tile, batch)
+    dev = gs[0].rho.device
+    if outs is None:
+        outs = [torch.empty((3, v.out_h, v.out_w), dtype=torch.float32, device=dev) for v in views]
+    for o, v in zip(outs, views):
+        if o.dtype != torch.float32 or not o.is_contiguous() or tuple(o.shape) != (3, v.out_h, v.out_w):
+            raise ValueError("outputs must be contiguous float32 [3, out_h, out_w]")
+    if ws is None:
+        ws = make_workspace(gs, views, None, tile, batch, stream=stream)
+    P = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+    _abi.check(_abi.load().gs_render_batched(n, G, V, P, ws.ptr, ws.nbytes, _stream(stream)),
+               "gs_render_batched")
+    if check:
+        sync_status(ws, stream)
+    return outs, ws
+
+
+def render_batched_bwd(gs, views, grad_outs, ws: Workspace, grads=None, tile=0, batch=0,
+                       stream=None, check: bool = False):
+    """Adjoint of the last render_batched on ws. Returns a list of [N_i, 9] float32."""
+    n, G, V = _arrays(gs, views, tile, batch)
+    dev = gs[0].rho.device
+    grad_outs = [g.contiguous().float() for g in grad_outs]
+    for go, v in zip(grad_outs, views):
+        if tuple(go.shape) != (3, v.out_h, v.out_w):
+            raise ValueError("grad_out must be [3, out_h, out_w]")
+    if grads is None:
+        grads = [torch.empty((g.n, 9), dtype=torch.float32, device=dev) for g in gs]
+    GO = (ctypes.c_void_p * n)(*[g.data_ptr() for g in grad_outs])
+    GR = (ctypes.c_void_p * n)(*[g.data_ptr() for g in grads])
+    _abi.check(_abi.load().gs_render_batched_bwd(n, G, V, GO, GR, ws.ptr, ws.nbytes,
+                                                 _stream(stream)), "gs_render_batched_bwd")
+    if check:
+        sync_status(ws, stream)
+    return grads
+
+
+def render(g: Gaussians, view, out=None, ws=None, tile=0, batch=0, stream=None, check=False):
+    outs, ws = render_batched([g], [view], None if out is None else [out], ws, tile, batch,
+                              stream, check)
+    return outs[0], ws
+
+
+def render_bwd(g: Gaussians, view, grad_out, ws, grads=None, tile=0, batch=0, stream=None,
+               check=False):
+    return render_batched_bwd([g], [view], [grad_out], ws, None if grads is None else [grads],
+                              tile, batch, stream, check)[0]
+
+
+def render_single_fwd(g: Gaussians, view, out, ws: Workspace, tile=0, batch=0, stream=None):
+    """Forward through the single-image entry point gs_render_fwd."""
+    G = _struct_g(g)
+    V = _struct_v(view, tile, batch)
+    _abi.check(_abi.load().gs_render_fwd(ctypes.byref(G), ctypes.byref(V), out.data_ptr(),
+                                         ws.ptr, ws.nbytes, _stream(stream)), "gs_render_fwd")
+    return out
+
+
+def render_single_bwd(g: Gaussians, view, grad_out, grads, ws: Workspace, tile=0, batch=0,
+                      stream=None):
+    """Adjoint through the single-image entry point gs_render_bwd."""
+    G = _struct_g(g)
+    V = _struct_v(view, tile, batch)
+    _abi.check(_abi.load().gs_render_bwd(ctypes.byref(G), ctypes.byref(V), grad_out.data_ptr(),
+                                         grads.data_ptr(), ws.ptr, ws.nbytes, _stream(stream)),
+               "gs_render_bwd")
+    return grads
+
+
+def sync_status(ws: Workspace, stream=None):
+    """Raise GsError if the kernels flagged a device-side problem (resets it)."""
+    _abi.check(_abi.load().gs_sync_status(ws.ptr, _stream(stream)), "device status")
+
+
+def read_stats(ws: Workspace, stream=None) -> dict:
+    st = _abi.GsStats()
+    _abi.check(_abi.load().gs_read_stats(ws.ptr, _stream(stream), ctypes.byref(st)), "gs_read_stats")
+    return {f: getattr(st, f) for f, _ in _abi.GsStats._fields_}
+
+
+def launch_count() -> int:
+    return int(_abi.load().gs_launch_count())
+
+
+# --------------------------------------------------------------------------
+# Autograd (differentiable rendering, Sec. 3.1 "Fast Rasterization" and
+# Sec. 3.2 "Rendering": the L1 loss is back-propagated through the render).
+# Per-pixel weights are recomputed in the backward, never stored.
+# --------------------------------------------------------------------------
+def _split_grads(gr: torch.Tensor, dtype):
+    return (gr[:, 0:2].to(dtype), gr[:, 2:4].to(dtype), gr[:, 4].to(dtype),
+            gr[:, 5:8].to(dtype), gr[:, 8].to(dtype))
+
+
+class GSRender(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, offset, sigma, rho, rgb, alpha, view, ref_grid_m: int = 1):
+        g = Gaussians(offset.contiguous(), sigma.contiguous(), rho.contiguous(), rgb.contiguous(),
+                      alpha.contiguous(), ref_grid_m)
+        out, ws = render(g, view)
+        ctx.g, ctx.view, ctx.ws = g, view, ws
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        gr = render_bwd(ctx.g, ctx.view, grad_out, ctx.ws)
+        return (*_split_grads(gr, ctx.g.offset.dtype), None, None)
+
+
+class GSRenderBatched(torch.autograd.Function):
+    """Images of uneven sizes and scales in one launch chain. Parameters are
+    concatenated over images; sizes[i] Gaussians belong to image i."""
+
+    @staticmethod
+    def forward(ctx, views, ref_grid_m, sizes, offset, sigma, rho, rgb, alpha):
+        gs, o = [], 0
+        ts = [t.contiguous() for t in (offset, sigma, rho, rgb, alpha)]
+        for n in sizes:
+            gs.append(Gaussians(*[t[o:o + n] for t in ts], ref_grid_m=ref_grid_m))
+            o += n
+        outs, ws = render_batched(gs, views)
+        ctx.gs, ctx.views, ctx.ws, ctx.dtype = gs, views, ws, offset.dtype
+        return tuple(outs)
+
+    @staticmethod
+    def backward(ctx, *grad_outs):
+        go = [torch.zeros((3, v.out_h, v.out_w), device=ctx.gs[0].rho.device) if g is None else g
+              for g, v in zip(grad_outs, ctx.views)]
+        grads = render_batched_bwd(ctx.gs, ctx.views, go, ctx.ws)
+        gr = torch.cat(grads, 0)
+        return (None, None, None, *_split_grads(gr, ctx.dtype))
+
+
+class Plan:
+    """A prepared render of fixed images: the ctypes arguments, the workspace
+    and the output / gradient buffers are built once, so each call costs one
+    C-ABI call. Fill `grad_outs` (or pass your own) before calling bwd().
+    The calls are asynchronous and can be captured in a CUDA graph."""
+
+    def __init__(self, gs, views, tile=0, batch=0, capacity=None, slack: float = 0.0,
+                 with_grads: bool = True, stream=None):
+        self.gs, self.views = list(gs), list(views)
+        self.n, self.G, self.V = _arrays(self.gs, self.views, tile, batch)
+        dev = self.gs[0].rho.device
+        self.ws = make_workspace(self.gs, self.views, capacity, tile, batch, slack, stream)
+        self.outs = [torch.empty((3, v.out_h, v.out_w), dtype=torch.float32, device=dev)
+                     for v in self.views]
+        self.P_out = (ctypes.c_void_p * self.n)(*[o.data_ptr() for o in self.outs])
+        self.lib = _abi.load()
+        if with_grads:
+            self.grad_outs = [torch.zeros_like(o) for o in self.outs]
+            self.grads = [torch.empty((g.n, 9), dtype=torch.float32, device=dev) for g in self.gs]
+            self.P_go = (ctypes.c_void_p * self.n)(*[g.data_ptr() for g in self.grad_outs])
+            self.P_gr = (ctypes.c_void_p * self.n)(*[g.data_ptr() for g in self.grads])
+
+    def fwd(self, stream=None):
+        st = self.lib.gs_render_batched(self.n, self.G, self.V, self.P_out, self.ws.ptr,
+                                        self.ws.nbytes, _stream(stream))
+        if st:
+            _abi.check(st, "gs_render_batched")
+        return self.outs
+
+    def bwd(self, stream=None):
+        st = self.lib.gs_render_batched_bwd(self.n, self.G, self.V, self.P_go, self.P_gr,
+                                            self.ws.ptr, self.ws.nbytes, _stream(stream))
+        if st:
+            _abi.check(st, "gs_render_batched_bwd")
+        return self.grads
+
+    def status(self, stream=None):
+        sync_status(self.ws, stream)
+
+    def stats(self, stream=None) -> dict:
+        return read_stats(self.ws, stream)
+
+
+def timing_enable(kernel_names=None):
+    """Per-kernel CUDA-event timing of the named kernels (None: all; []: off)."""
+    lib = _abi.load()
+    if kernel_names is None:
+        mask = -1
+    else:
+        ids = {lib.gs_kernel_name(i).decode(): i for i in range(32) if lib.gs_kernel_name(i)}
+        mask = 0
+        for k in kernel_names:
+            mask |= 1 << ids[k]
+    _abi.check(lib.gs_timing_enable(mask), "gs_timing_enable")
+
+
+def timing_read() -> dict:
+    """{kernel name: (total ms, launches)} since the last read (synchronises)."""
+    lib = _abi.load()
+    ms = (ctypes.c_double * 32)()
+    cnt = (ctypes.c_int64 * 32)()
+    n = lib.gs_timing_read(ms, cnt, 32)
+    return {lib.gs_kernel_name(i).decode(): (ms[i], cnt[i]) for i in range(n) if cnt[i]}
