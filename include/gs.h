@@ -151,6 +151,28 @@ gs_status gs_render_batched_bwd(int32_t n_images, const gs_gaussians* g, const g
                                 const float* const* grad_outs, float* const* grads, void* ws,
                                 size_t ws_bytes, void* stream);
 
+/* Forward render like gs_render_fwd, for callers that cannot allocate device
+ * memory and so cannot supply a workspace: a plugin whose host framework owns
+ * all device memory and passes it only input and output pointers, or a
+ * real-time loop that must not call cudaMalloc. The GSASR paper has no
+ * counterpart to this call; it only changes where the scratch lives.
+ *   - Scratch: one static 64 MiB array in device memory (held by every device
+ *     that loads libgs.so until the process exits). Renders that need more,
+ *     for the per-Gaussian state (about 130 bytes per Gaussian) or for the
+ *     (tile, Gaussian) pairs (16 bytes each), are rejected with
+ *     GS_ERR_UNSUPPORTED and a message saying how much they need.
+ *   - The first call with a given device current looks up the array's device
+ *     address (cudaGetSymbolAddress); make that first call before any stream
+ *     capture.
+ *   - Each call counts the pairs first, synchronising `stream`, then launches
+ *     the render asynchronously on `stream`.
+ *   - All calls share the one array and each leaves its state there: calls
+ *     that overlap on the GPU (other streams, other host threads) race and
+ *     give wrong images. gs_render_bwd cannot follow this call.
+ * g, v, out: as for gs_render_fwd (device parameters, device output). */
+gs_status gs_render_fwd_noalloc(const gs_gaussians* g, const gs_view* v, float* out,
+                                void* stream);
+
 /* Synchronises `stream`, returns the workspace's device status word and resets
  * it to GS_OK. */
 gs_status gs_sync_status(void* ws, void* stream);

@@ -21,7 +21,7 @@ GS_NORM_DENSITY, GS_NORM_PEAK = 0, 1
 EXPORTS = ("gs_workspace_size", "gs_count_pairs", "gs_render_fwd", "gs_render_bwd",
            "gs_render_batched", "gs_render_batched_bwd", "gs_sync_status", "gs_read_stats",
            "gs_last_error", "gs_status_string", "gs_launch_count", "gs_timing_enable",
-           "gs_timing_read", "gs_kernel_name", "gs_version")
+           "gs_timing_read", "gs_kernel_name", "gs_version", "gs_render_fwd_noalloc")
 
 
 class GsGaussians(ctypes.Structure):
@@ -88,6 +88,7 @@ def load(path: str | None = None):
             "gs_timing_read": (i32, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64), i32]),
             "gs_kernel_name": (ctypes.c_char_p, [i32]),
             "gs_version": (ctypes.c_char_p, []),
+            "gs_render_fwd_noalloc": (i32, [G, V, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)

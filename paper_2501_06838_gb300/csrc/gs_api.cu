@@ -348,6 +348,8 @@ const char* status_text(uint32_t bits) {
 
 namespace gs {
 
+void set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
 void launch_begin(int id, cudaStream_t s) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
   if (!((g_timing_mask.load(std::memory_order_relaxed) >> id) & 1u)) return;
