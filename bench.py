@@ -227,6 +227,15 @@ def run_gpu(args, rank, world, local_rank):
         total_ms = float(t.item())
     plan.status()
 
+    # ---- per-stage breakdown (after the timed region, every kernel timed) ----
+    gs.timing_enable(None)
+    for _ in range(3):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    gs.timing_enable([])
+    stage = {k: round(v[0] / 3, 5) for k, v in gs.timing_read().items()}
+
     # ---- roofline of the dominant kernel ----
     peaks, peak_src = load_peaks()
     f_clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
@@ -257,6 +266,7 @@ def run_gpu(args, rank, world, local_rank):
                    "parallelism": f"replicas x{world} (one full workload per GPU)"},
         "fwd_mpix_s": round(hr_pix * args.steps / (sum(fwd_ms) * 1e-3) / 1e6, 2),
         "kernel_ms": {k: round(v[0] / v[1], 5) for k, v in ktimes.items()},
+        "stage_ms_per_step": stage,
         "pairs": {"pixel_pairs": stats["pixel_pairs"], "tile_pairs": stats["tile_pairs"]},
         "roofline": roof, "gpu_launches": int(launches), "clocks": clk,
     }

@@ -16,7 +16,6 @@
 namespace gs {
 int scan_parts_needed(int64_t n);
 int sort_blocks_needed(int64_t capacity);
-size_t raster_smem_bytes(int tile, int batch, int bwd);
 }  // namespace gs
 
 namespace {
