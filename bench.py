@@ -36,15 +36,18 @@ import gs_synthetic as S  # noqa: E402
 METRIC = "HR Mpix/s fwd and fwd+bwd at ×4/×12 vs FP64 oracle error; % FP32/SFU peak"
 UNIT = "HR Mpix/s"
 
-# ALU roofline of the raster kernels (derivation in the design doc): every FP32 and
-# MUFU instruction takes one issue slot; an SM issues 4 warp-instructions per
-# clock = 128 lane-instructions. The irreducible per-pair work is
-#   forward: 1 FFMA (exponent, row terms hoisted) + 1 MUFU.EX2 + 3 FFMA (RGB)  = 5
-#   adjoint: forward's 2 + 3 (colour grads) + 3 (g.c) + 1 (G w) + 3 (Y moments) = 12
-# MUFU.EX2 issues at 32 lanes/clk/SM on GB300 (probe), so issue binds first.
+# ALU roofline of the raster kernels (derivation in the design doc). Measured on
+# GB300 with a probe: an SM issues 4 warp-instructions per clock; MUFU.EX2 runs
+# at 32 lanes/clk/SM and holds its scheduler for 4 issue cycles per warp
+# instruction; FP32 work can be packed two-wide (FFMA2/FADD2/FMUL2). Per
+# (Gaussian, pixel) pair the method needs 1 exp2 and
+#   forward: 5 FP32 ops (exponent 2, colour 3)               -> 4 + 5/2  = 6.5 cycles
+#   adjoint: 12 FP32 ops (exponent 2, g.c 3, G w Y 2, Y      -> 4 + 12/2 = 10 cycles
+#            moments 2, colour grads 3)
+# per warp of 32 pairs, so peak pairs/clk/SM = 4 * 32 / cycles.
 SMS = 152
-ISSUE_PER_SM_CLK = 128
-PAIR_COST = {"raster_fwd": 5, "raster_bwd": 12}
+WARP_ISSUE_PER_SM_CLK = 4
+PAIR_CYCLES = {"raster_fwd": 6.5, "raster_bwd": 10.0}
 
 
 def load_peaks():
@@ -246,12 +249,13 @@ def run_gpu(args, rank, world, local_rank):
         per_launch_s = ms / cnt * 1e-3
         pairs = stats["pixel_pairs"]
         achieved = pairs / per_launch_s / 1e9
-        peak = SMS * f_clk * ISSUE_PER_SM_CLK / PAIR_COST[dom] / 1e9
+        peak = SMS * f_clk * WARP_ISSUE_PER_SM_CLK * 32 / PAIR_CYCLES[dom] / 1e9
         roof = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 2),
                 "peak": round(peak, 2), "unit": "Gpair/s", "frac": round(achieved / peak, 4),
                 "traffic": None,
-                "peak_basis": (f"{SMS} SMs x {ISSUE_PER_SM_CLK} issue/clk x {f_clk / 1e6:.0f} MHz "
-                               f"/ {PAIR_COST[dom]} instr per pair ({peak_src} sm_max_mhz)"),
+                "peak_basis": (f"{SMS} SMs x {WARP_ISSUE_PER_SM_CLK} warp-issue/clk x 32 x "
+                               f"{f_clk / 1e6:.0f} MHz / {PAIR_CYCLES[dom]} issue cycles per warp "
+                               f"of pairs ({peak_src} sm_max_mhz)"),
                 "pairs_per_launch": pairs, "ms_per_launch": round(ms / cnt, 5)}
 
     res = {

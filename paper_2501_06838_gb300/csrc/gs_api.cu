@@ -107,7 +107,7 @@ Layout make_layout(int n_images, int64_t n, int64_t tiles, int64_t capacity) {
 }
 
 int tile_of(const gs_view& v) { return v.tile == 0 ? 16 : v.tile; }
-int batch_of(const gs_view& v) { return v.batch == 0 ? 64 : v.batch; }
+int batch_of(const gs_view& v) { return v.batch == 0 ? 32 : v.batch; }
 int shift_of(int tile) { return tile == 8 ? 3 : tile == 32 ? 5 : 4; }
 
 struct Problem {

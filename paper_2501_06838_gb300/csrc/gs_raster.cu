@@ -11,15 +11,18 @@
 //   stage 1: one thread per Gaussian moves its centre into tile-local
 //            coordinates (cx - x_tile: small numbers, so X = x - cx keeps full
 //            float32 precision even at x ~ 5760) and clips its window;
-//   stage 2: per (Gaussian, tile row) the row terms of the exponent
+//   stage 2: per (Gaussian, pair of tile rows) the row terms of the exponent
 //              e = -(sA X - sK Y)^2 + g Y^2 + l        (log2 units)
-//            rowK = sK*Y, rowG = g*Y^2 + l  (rowG = -inf outside the window rows);
+//            as one float4 (-K(r), -K(r+1), R(r), R(r+1)) with K = sK*Y and
+//            R = g*Y^2 + l (R = -inf outside the window rows);
 //   compute: per Gaussian each thread forms Xs = sA*(col - cxl) (+inf outside
-//            the window columns) and, per owned pixel,
-//              d = Xs - rowK, e = -d*d + rowG, w = 2^e (MUFU.EX2), out += c*w,
-//            i.e. 1 FADD + 1 FFMA + 1 MUFU + 3 FFMA per (Gaussian, pixel) pair.
-//            The next Gaussian's shared-memory operands are loaded while the
-//            current one is computed.
+//            the window columns) and, for each of its row pairs, in packed
+//            FP32x2 arithmetic (one instruction for both rows),
+//              d = Xs - K, e = R - d*d, w = 2^e (MUFU.EX2, one per pixel),
+//              out += c*w  (three FFMA2 for the three channels),
+//            i.e. per pixel 2.5 FP32 instructions + 1 MUFU. The next
+//            Gaussian's shared-memory operands load while the current one
+//            is computed.
 // The window masks are folded into the exponent: -inf rows and +inf columns
 // both give e = -inf and w = +0, so masked pairs cost no branch. The completed
 // square has no cancellation for any |rho| < 1 (the Y term is the marginal).
@@ -93,30 +96,66 @@ __device__ __forceinline__ void stage_records(const float4* raw, int nb, int ox,
   }
 }
 
-// Stage 2: row terms (rowK, rowG[, Y]) of every staged Gaussian and tile row.
-template <int TILE, int NT, bool WITH_Y>
-__device__ __forceinline__ void stage_rows(int nb, const float4* gB, const float4* gC, void* rows) {
-  for (int idx = threadIdx.x; idx < nb * TILE; idx += NT) {
-    const int i = idx / TILE, r = idx - i * TILE;
+// Stage 2: row terms of every staged Gaussian and pair of tile rows, as
+// (-K(2p), -K(2p+1), R(2p), R(2p+1)).
+template <int TILE, int NT>
+__device__ __forceinline__ void stage_rowpairs(int nb, const float4* gB, const float4* gC,
+                                               float4* rq) {
+  constexpr int HP = TILE / 2;
+  for (int idx = threadIdx.x; idx < nb * HP; idx += NT) {
+    const int i = idx / HP, p = idx - i * HP;
     const float4 b = gB[i];
     const int pk = __float_as_int(gC[i].w);
-    const float Y = (float)r - b.x;
-    float rowG = fmaf(b.z * Y, Y, b.w);
-    if (r < (pk & 0xffff) || r > (pk >> 16)) rowG = -kInf;
-    if (WITH_Y) {
-      reinterpret_cast<float4*>(rows)[idx] = make_float4(b.y * Y, rowG, Y, 0.0f);
-    } else {
-      reinterpret_cast<float2*>(rows)[idx] = make_float2(b.y * Y, rowG);
-    }
+    const int ly0 = pk & 0xffff, ly1 = pk >> 16;
+    const int r0 = 2 * p, r1 = 2 * p + 1;
+    const float Y0 = (float)r0 - b.x, Y1 = (float)r1 - b.x;
+    float R0 = fmaf(b.z * Y0, Y0, b.w), R1 = fmaf(b.z * Y1, Y1, b.w);
+    if (r0 < ly0 || r0 > ly1) R0 = -kInf;
+    if (r1 < ly0 || r1 > ly1) R1 = -kInf;
+    rq[idx] = make_float4(-b.y * Y0, -b.y * Y1, R0, R1);
+  }
+}
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+// Shared-memory operands of one Gaussian for one thread: gA, gC and the row
+// terms of its NQ = BY / 2 row pairs.
+template <int NQ>
+struct FwdOps {
+  float4 a, c, q[NQ];
+  __device__ __forceinline__ void load(const float4* gA, const float4* gC, const float4* rq,
+                                       int i, int hp, int pair0) {
+    a = gA[i];
+    c = gC[i];
+    const float4* rr = rq + i * hp + pair0;
+#pragma unroll
+    for (int j = 0; j < NQ; ++j) q[j] = rr[j];
+  }
+};
+
+template <int NQ>
+__device__ __forceinline__ void fwd_gaussian(float2 (&acc)[NQ][3], const FwdOps<NQ>& o, float fcol) {
+  float Xs = o.a.y * (fcol - o.a.x);
+  if (fcol < o.a.z || fcol > o.a.w) Xs = kInf;
+  const float2 X2 = f2(Xs, Xs);
+  const float2 c0 = f2(o.c.x, o.c.x), c1 = f2(o.c.y, o.c.y), c2 = f2(o.c.z, o.c.z);
+#pragma unroll
+  for (int j = 0; j < NQ; ++j) {
+    const float2 d = __fadd2_rn(X2, f2(o.q[j].x, o.q[j].y));
+    const float2 e = __ffma2_rn(f2(-d.x, -d.y), d, f2(o.q[j].z, o.q[j].w));
+    const float2 wv = f2(ex2_approx(e.x), ex2_approx(e.y));
+    acc[j][0] = __ffma2_rn(c0, wv, acc[j][0]);
+    acc[j][1] = __ffma2_rn(c1, wv, acc[j][1]);
+    acc[j][2] = __ffma2_rn(c2, wv, acc[j][2]);
   }
 }
 
 template <int TILE, int BY, int PF>
 __global__ void __launch_bounds__(TILE * TILE / BY) k_raster_fwd(Ws w, const uint32_t* vals) {
-  constexpr int NT = TILE * TILE / BY, BATCH = NT * PF, NQ = BY / 2;
+  constexpr int NT = TILE * TILE / BY, BATCH = NT * PF, NQ = BY / 2, HP = TILE / 2;
   __shared__ __align__(16) float4 raw[2][BATCH * kRecordF4];
   __shared__ float4 gA[BATCH], gB[BATCH], gC[BATCH];
-  __shared__ __align__(16) float2 rows[BATCH * TILE];
+  __shared__ float4 rq[BATCH * HP];
 
   const ImageDesc* D;
   int ox, oy;
@@ -124,11 +163,12 @@ __global__ void __launch_bounds__(TILE * TILE / BY) k_raster_fwd(Ws w, const uin
   const uint2 range = w.ranges[blockIdx.x];
   const int col = threadIdx.x % TILE;
   const int row0 = (threadIdx.x / TILE) * BY;
+  const int pair0 = row0 / 2;
   const float fcol = (float)col;
 
-  float acc[BY][3];
+  float2 acc[NQ][3];
 #pragma unroll
-  for (int k = 0; k < BY; ++k) acc[k][0] = acc[k][1] = acc[k][2] = 0.0f;
+  for (int j = 0; j < NQ; ++j) acc[j][0] = acc[j][1] = acc[j][2] = f2(0.0f, 0.0f);
 
   const int start = (int)range.x, total = (int)range.y - start;
   const int nbat = (total + BATCH - 1) / BATCH;
@@ -144,47 +184,22 @@ __global__ void __launch_bounds__(TILE * TILE / BY) k_raster_fwd(Ws w, const uin
     __syncthreads();
     stage_records<TILE, NT>(raw[b & 1], nb, ox, oy, gA, gB, gC);
     __syncthreads();
-    stage_rows<TILE, NT, false>(nb, gB, gC, rows);
+    stage_rowpairs<TILE, NT>(nb, gB, gC, rq);
     __syncthreads();
     if (b + 1 < nbat) {
       issue_records<NT, PF>(w, gid, min(BATCH, total - (b + 1) * BATCH), raw[(b + 1) & 1]);
       if (b + 2 < nbat)
         load_ids<NT, PF>(vals, start + (b + 2) * BATCH, min(BATCH, total - (b + 2) * BATCH), gid);
     }
-    // software pipeline: operands of Gaussian i + 1 load while i computes
-    float4 a = gA[0], c = gC[0];
-    float4 q[NQ];
-    {
-      const float4* rr = reinterpret_cast<const float4*>(rows + row0);
-#pragma unroll
-      for (int j = 0; j < NQ; ++j) q[j] = rr[j];
-    }
-    for (int i = 0; i < nb; ++i) {
-      const int inext = min(i + 1, nb - 1);
-      const float4 an = gA[inext], cn = gC[inext];
-      float4 qn[NQ];
-      const float4* rr = reinterpret_cast<const float4*>(rows + inext * TILE + row0);
-#pragma unroll
-      for (int j = 0; j < NQ; ++j) qn[j] = rr[j];
-      float Xs = a.y * (fcol - a.x);
-      if (fcol < a.z || fcol > a.w) Xs = kInf;
-#pragma unroll
-      for (int j = 0; j < NQ; ++j) {
-        const float d0 = Xs - q[j].x;
-        const float w0 = ex2_approx(fmaf(-d0, d0, q[j].y));
-        const float d1 = Xs - q[j].z;
-        const float w1 = ex2_approx(fmaf(-d1, d1, q[j].w));
-        acc[2 * j][0] = fmaf(c.x, w0, acc[2 * j][0]);
-        acc[2 * j][1] = fmaf(c.y, w0, acc[2 * j][1]);
-        acc[2 * j][2] = fmaf(c.z, w0, acc[2 * j][2]);
-        acc[2 * j + 1][0] = fmaf(c.x, w1, acc[2 * j + 1][0]);
-        acc[2 * j + 1][1] = fmaf(c.y, w1, acc[2 * j + 1][1]);
-        acc[2 * j + 1][2] = fmaf(c.z, w1, acc[2 * j + 1][2]);
-      }
-      a = an;
-      c = cn;
-#pragma unroll
-      for (int j = 0; j < NQ; ++j) q[j] = qn[j];
+    // Two operand sets in registers: Gaussian i + 1's loads overlap i's math.
+    FwdOps<NQ> A, B;
+    A.load(gA, gC, rq, 0, HP, pair0);
+    for (int i = 0; i < nb; i += 2) {
+      if (i + 1 < nb) B.load(gA, gC, rq, i + 1, HP, pair0);
+      fwd_gaussian<NQ>(acc, A, fcol);
+      if (i + 1 >= nb) break;
+      if (i + 2 < nb) A.load(gA, gC, rq, i + 2, HP, pair0);
+      fwd_gaussian<NQ>(acc, B, fcol);
     }
     __syncthreads();
   }
@@ -199,32 +214,90 @@ __global__ void __launch_bounds__(TILE * TILE / BY) k_raster_fwd(Ws w, const uin
       const int y = oy + row0 + k;
       if (y < H) {
         const int64_t o = (int64_t)y * W + x;
-        out[o] = acc[k][0];
-        out[plane + o] = acc[k][1];
-        out[2 * plane + o] = acc[k][2];
+        const int j = k / 2;
+        out[o] = (k & 1) ? acc[j][0].y : acc[j][0].x;
+        out[plane + o] = (k & 1) ? acc[j][1].y : acc[j][1].x;
+        out[2 * plane + o] = (k & 1) ? acc[j][2].y : acc[j][2].x;
       }
     }
   }
 }
 
 // Adjoint. Each thread holds dL/dI of its pixels; per staged Gaussian it
-// accumulates, over its pixels, Gw = (g . c) 2^e and the moments
-//   S0 = sum Gw, SY = sum Gw Y, SYY = sum Gw Y^2, C_k = sum g_k 2^e,
-// then (its X is fixed) SX = X S0, SXX = X SX, SXY = X SY.
+// accumulates, over its pixels, with Gw = (g . c) 2^e,
+//   SY = sum Gw Y, SYY = sum Gw Y^2, C_k = sum g_k 2^e,
+// and forms S0 = sum Gw = c . C, then (its X is fixed) SX = X S0, SXX = X SX,
+// SXY = X SY. Y = y - cy is rebuilt per pixel from the thread's first row.
 // Reduction over each warp's 32 lanes, batched over kRB Gaussians: lanes store
 // their nine values transposed in shared memory (row (g, f) holds the 32 lane
 // values, padded to 33 floats so that no two lanes read one bank), then lane j
 // sums rows j, j + 32, ... and adds each total to the Gaussian's record-space
 // accumulator: one atomic per (tile, Gaussian, value) and warp.
-constexpr int kRB = 8;            // Gaussians per reduction round
+constexpr int kRB = 4;            // Gaussians per reduction round
 constexpr int kRedRow = 33;       // padded row of 32 lane values
+
+template <int NQ>
+struct BwdOps {
+  float4 a, c, q[NQ];
+  float cy;
+  __device__ __forceinline__ void load(const float4* gA, const float4* gB, const float4* gC,
+                                       const float4* rq, int i, int hp, int pair0) {
+    a = gA[i];
+    c = gC[i];
+    cy = gB[i].x;
+    const float4* rr = rq + i * hp + pair0;
+#pragma unroll
+    for (int j = 0; j < NQ; ++j) q[j] = rr[j];
+  }
+};
+
+// The nine record-space moments of one Gaussian over this thread's pixels,
+// two rows at a time in packed FP32x2 arithmetic. g[j][ch] holds dL/dI of
+// channel ch at rows (2j, 2j + 1).
+template <int NQ>
+__device__ __forceinline__ void bwd_gaussian(const float2 (&g)[NQ][3], const BwdOps<NQ>& o,
+                                             float fcol, int row0, float (&v)[9]) {
+  const float Xr = fcol - o.a.x;
+  const float Xs = (fcol < o.a.z || fcol > o.a.w) ? kInf : o.a.y * Xr;
+  const float2 X2 = f2(Xs, Xs);
+  const float Y0 = (float)row0 - o.cy;
+  const float2 Yb = f2(Y0, Y0 + 1.0f);
+  const float2 cr = f2(o.c.x, o.c.x), cg = f2(o.c.y, o.c.y), cb = f2(o.c.z, o.c.z);
+  float2 SY = f2(0.f, 0.f), SYY = SY, Cr = SY, Cg = SY, Cb = SY;
+#pragma unroll
+  for (int j = 0; j < NQ; ++j) {
+    const float2 Y = __fadd2_rn(Yb, f2(2.0f * j, 2.0f * j));
+    const float2 d = __fadd2_rn(X2, f2(o.q[j].x, o.q[j].y));
+    const float2 e = __ffma2_rn(f2(-d.x, -d.y), d, f2(o.q[j].z, o.q[j].w));
+    const float2 wv = f2(ex2_approx(e.x), ex2_approx(e.y));
+    const float2 G = __ffma2_rn(g[j][2], cb, __ffma2_rn(g[j][1], cg, __fmul2_rn(g[j][0], cr)));
+    const float2 GwY = __fmul2_rn(__fmul2_rn(G, wv), Y);
+    SY = __fadd2_rn(SY, GwY);
+    SYY = __ffma2_rn(GwY, Y, SYY);
+    Cr = __ffma2_rn(g[j][0], wv, Cr);
+    Cg = __ffma2_rn(g[j][1], wv, Cg);
+    Cb = __ffma2_rn(g[j][2], wv, Cb);
+  }
+  const float cR = Cr.x + Cr.y, cG = Cg.x + Cg.y, cB = Cb.x + Cb.y;
+  const float S0 = fmaf(o.c.z, cB, fmaf(o.c.y, cG, o.c.x * cR));
+  const float sy = SY.x + SY.y;
+  v[0] = S0;
+  v[1] = Xr * S0;
+  v[2] = sy;
+  v[3] = Xr * v[1];
+  v[4] = Xr * sy;
+  v[5] = SYY.x + SYY.y;
+  v[6] = cR;
+  v[7] = cG;
+  v[8] = cB;
+}
 
 template <int TILE, int BY, int PF>
 __global__ void __launch_bounds__(TILE * TILE / BY) k_raster_bwd(Ws w, const uint32_t* vals) {
-  constexpr int NT = TILE * TILE / BY, NW = NT / 32, BATCH = NT * PF;
+  constexpr int NT = TILE * TILE / BY, NW = NT / 32, BATCH = NT * PF, NQ = BY / 2, HP = TILE / 2;
   __shared__ __align__(16) float4 raw[2][BATCH * kRecordF4];
   __shared__ float4 gA[BATCH], gB[BATCH], gC[BATCH];
-  __shared__ __align__(16) float4 rows[BATCH * TILE];
+  __shared__ float4 rq[BATCH * HP];
   __shared__ float red[NW][kRB * 9 * kRedRow];
   __shared__ uint32_t gids[2][BATCH];
 
@@ -235,6 +308,7 @@ __global__ void __launch_bounds__(TILE * TILE / BY) k_raster_bwd(Ws w, const uin
   if (range.y <= range.x) return;
   const int col = threadIdx.x % TILE;
   const int row0 = (threadIdx.x / TILE) * BY;
+  const int pair0 = row0 / 2;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float fcol = (float)col;
   float* wred = red[warp];
@@ -242,7 +316,7 @@ __global__ void __launch_bounds__(TILE * TILE / BY) k_raster_bwd(Ws w, const uin
   const int wrow0 = ((threadIdx.x & ~31) / TILE) * BY;
   const int wrow1 = min(TILE - 1, (((threadIdx.x | 31) / TILE) + 1) * BY - 1);
 
-  float g[BY][3];
+  float2 g[NQ][3];
   {
     const int H = D->out_h, W = D->out_w;
     const int x = ox + col;
@@ -252,9 +326,10 @@ __global__ void __launch_bounds__(TILE * TILE / BY) k_raster_bwd(Ws w, const uin
       const int y = oy + row0 + k;
       const bool in = x < W && y < H;
       const int64_t o = (int64_t)y * W + x;
-      g[k][0] = in ? __ldg(D->grad_out + o) : 0.0f;
-      g[k][1] = in ? __ldg(D->grad_out + plane + o) : 0.0f;
-      g[k][2] = in ? __ldg(D->grad_out + 2 * plane + o) : 0.0f;
+      float* gk = reinterpret_cast<float*>(&g[k / 2][0]) + (k & 1);
+      gk[0] = in ? __ldg(D->grad_out + o) : 0.0f;
+      gk[2] = in ? __ldg(D->grad_out + plane + o) : 0.0f;
+      gk[4] = in ? __ldg(D->grad_out + 2 * plane + o) : 0.0f;
     }
   }
 
@@ -273,7 +348,7 @@ __global__ void __launch_bounds__(TILE * TILE / BY) k_raster_bwd(Ws w, const uin
     __syncthreads();
     stage_records<TILE, NT>(raw[b & 1], nb, ox, oy, gA, gB, gC);
     __syncthreads();
-    stage_rows<TILE, NT, true>(nb, gB, gC, rows);
+    stage_rowpairs<TILE, NT>(nb, gB, gC, rq);
     __syncthreads();
     if (b + 1 < nbat) {
 #pragma unroll
@@ -283,41 +358,13 @@ __global__ void __launch_bounds__(TILE * TILE / BY) k_raster_bwd(Ws w, const uin
         load_ids<NT, PF>(vals, start + (b + 2) * BATCH, min(BATCH, total - (b + 2) * BATCH), gid);
     }
     const uint32_t* bgid = gids[b & 1];
-    for (int i = 0; i < nb; ++i) {
-      const float4 c = gC[i];
+    // One Gaussian: its moments, staged for the warp reduction; every kRB
+    // Gaussians (and at the end of the batch) the warp reduces and adds.
+    auto process = [&](const BwdOps<NQ>& o, int i) {
       float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      const int pk = __float_as_int(c.w);
-      if (NW == 1 || ((pk >> 16) >= wrow0 && (pk & 0xffff) <= wrow1)) {   // warp-uniform
-        const float4 a = gA[i];
-        const float Xr = fcol - a.x;
-        const float Xs = (fcol < a.z || fcol > a.w) ? kInf : a.y * Xr;
-        const float4* rr = rows + i * TILE + row0;
-        float S0 = 0.f, SY = 0.f, SYY = 0.f, Cr = 0.f, Cg = 0.f, Cb = 0.f;
-#pragma unroll
-        for (int k = 0; k < BY; ++k) {
-          const float4 q = rr[k];
-          const float dd = Xs - q.x;
-          const float wv = ex2_approx(fmaf(-dd, dd, q.y));
-          const float G = fmaf(g[k][2], c.z, fmaf(g[k][1], c.y, g[k][0] * c.x));
-          const float Gw = G * wv;
-          const float GwY = Gw * q.z;
-          S0 += Gw;
-          SY += GwY;
-          SYY = fmaf(GwY, q.z, SYY);
-          Cr = fmaf(g[k][0], wv, Cr);
-          Cg = fmaf(g[k][1], wv, Cg);
-          Cb = fmaf(g[k][2], wv, Cb);
-        }
-        v[0] = S0;
-        v[1] = Xr * S0;
-        v[2] = SY;
-        v[3] = Xr * v[1];
-        v[4] = Xr * SY;
-        v[5] = SYY;
-        v[6] = Cr;
-        v[7] = Cg;
-        v[8] = Cb;
-      }
+      const int pk = __float_as_int(o.c.w);
+      if (NW == 1 || ((pk >> 16) >= wrow0 && (pk & 0xffff) <= wrow1))   // warp-uniform
+        bwd_gaussian<NQ>(g, o, fcol, row0, v);
       const int slot = i % kRB;
 #pragma unroll
       for (int f = 0; f < 9; ++f) wred[(slot * 9 + f) * kRedRow + lane] = v[f];
@@ -340,6 +387,16 @@ __global__ void __launch_bounds__(TILE * TILE / BY) k_raster_bwd(Ws w, const uin
         }
         __syncwarp();
       }
+    };
+    // Two operand sets in registers: Gaussian i + 1's loads overlap i's math.
+    BwdOps<NQ> A, B;
+    A.load(gA, gB, gC, rq, 0, HP, pair0);
+    for (int i = 0; i < nb; i += 2) {
+      if (i + 1 < nb) B.load(gA, gB, gC, rq, i + 1, HP, pair0);
+      process(A, i);
+      if (i + 1 >= nb) break;
+      if (i + 2 < nb) A.load(gA, gB, gC, rq, i + 2, HP, pair0);
+      process(B, i + 1);
     }
     __syncthreads();
   }
