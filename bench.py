@@ -70,6 +70,8 @@ WORKLOADS = {
     "c4x12-f16": "LR 480x270, m=4 (N=518,400), x12 -> 5760x3240, forward + adjoint, FP16 params",
     "c4x12-f32": "LR 480x270, m=4 (N=518,400), x12 -> 5760x3240, forward + adjoint, FP32 params",
     "c3": "16 images, LR 64..480 x 64..360, m=1, s ~ U[1.5, 12], batched forward, FP32 params",
+    "c5": "training step: batch 16 of 48x48 LR crops, s ~ U[1, 4], 8-block 64-ch conv encoder + "
+          "1x1 Gaussian head, BF16 params, batched render fwd+bwd, L1 loss, Adam",
 }
 
 
@@ -296,6 +298,66 @@ def run_gpu(args, rank, world, local_rank):
     return res
 
 
+def run_train(args, rank, world, local_rank):
+    """Config 5: end-to-end training steps (encoder + head + render + loss +
+    backward + Adam); reports rendered HR Mpix/s, step time and the share of
+    the step spent in the library's kernels."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_2501_06838_gb300 as gs
+    from paper_2501_06838_gb300.train_step import TrainStep
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    step = TrainStep(device=dev)
+    lr, hrs, scales = S.config5_batch(rank)
+    lr_t = torch.from_numpy(lr).to(dev)
+    hr_t = [torch.from_numpy(h).to(dev) for h in hrs]
+    hr_pix = sum(h.shape[1] * h.shape[2] for h in hrs)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        step(lr_t, hr_t, scales)
+    torch.cuda.synchronize()
+    gs.timing_read()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = gs.launch_count()
+    gs.timing_enable(None)
+    tot = 0.0
+    loss = None
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        loss = step(lr_t, hr_t, scales)
+        b.record()
+        b.synchronize()
+        tot += a.elapsed_time(b)
+    gs.timing_enable([])
+    kt = gs.timing_read()
+    launches = gs.launch_count() - launches0
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([tot], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot = float(t.item())
+    render_ms = sum(v[0] for v in kt.values())
+    return {"metric": METRIC, "value": round(world * hr_pix * args.steps / (tot * 1e-3) / 1e6, 2),
+            "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(tot / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": f"c5: {WORKLOADS['c5']}", "hr_pixels_per_step": hr_pix,
+                       "scales": [round(s, 3) for s in scales],
+                       "l2": "flushed before every step (256 MiB write, outside the timed events)"},
+            "render_share": round(render_ms / tot, 4),
+            "render_ms_per_step": round(render_ms / args.steps, 4),
+            "kernel_ms_per_step": {k: round(v[0] / args.steps, 5) for k, v in kt.items()},
+            "final_loss": float(loss), "gpu_launches": int(launches), "clocks": clk}
+
+
 def run_e2e(args, plan, gsets, views, with_adj, dtname, dev, stream, flush):
     """Same metric through Plan.fwd/bwd, with every step copying its inputs from
     pinned host memory and its results back (copies inside the timed region)."""
@@ -482,7 +544,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     import __graft_entry__
     __graft_entry__.build()
-    res = run_gpu(args, rank, world, local_rank)
+    res = run_train(args, rank, world, local_rank) if args.workload == "c5" else \
+        run_gpu(args, rank, world, local_rank)
     if rank == 0:
         print(json.dumps(res), flush=True)
     if world > 1:

@@ -210,3 +210,62 @@ def config4(scale: float = 12.0, dtype: str = "bf16"):
 def config5_scales(seed: int = 0, batch: int = 16):
     rng = np.random.Generator(np.random.PCG64(seed))
     return [float(np.float32(s)) for s in rng.uniform(1.0, 4.0, size=batch)]
+
+
+# --------------------------------------------------------------------------
+# Config 5: a seeded continuous image function, sampled at the LR pixel
+# centres for the input crop and at (x/s, y/s) for the HR target (the sampling
+# convention of Eq. 4), so every scale factor has an exact target.
+# --------------------------------------------------------------------------
+@dataclasses.dataclass
+class ImageFunction:
+    freqs: np.ndarray    # [K, 2] cycles per LR pixel
+    phases: np.ndarray   # [K]
+    amps: np.ndarray     # [K, 3]
+    normals: np.ndarray  # [E, 2] unit edge normals
+    offsets: np.ndarray  # [E]
+    steps: np.ndarray    # [E, 3] colour jump across each edge
+    base: np.ndarray     # [3]
+
+    def __call__(self, x, y):
+        """x, y: arrays of LR coordinates; returns [3, *x.shape] in ~[0, 1]."""
+        x = np.asarray(x, dtype=np.float64)
+        y = np.asarray(y, dtype=np.float64)
+        out = np.zeros((3,) + x.shape)
+        for (fx, fy), ph, a in zip(self.freqs, self.phases, self.amps):
+            out += a[:, None, None] * np.cos(2 * np.pi * (fx * x + fy * y) + ph)[None]
+        for (nx, ny), d, st in zip(self.normals, self.offsets, self.steps):
+            ramp = 0.5 * (1 + np.tanh((nx * x + ny * y - d) / 0.5))
+            out += st[:, None, None] * ramp[None]
+        return np.clip(out + self.base[:, None, None], 0.0, 1.0)
+
+
+def image_function(seed: int, size: int = 48) -> ImageFunction:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    k, e = 12, 3
+    ang = rng.uniform(0, 2 * np.pi, k)
+    rad = rng.uniform(0.01, 0.15, k)
+    theta = rng.uniform(0, 2 * np.pi, e)
+    return ImageFunction(
+        freqs=np.stack([rad * np.cos(ang), rad * np.sin(ang)], 1),
+        phases=rng.uniform(0, 2 * np.pi, k),
+        amps=rng.normal(0, 0.08, (k, 3)),
+        normals=np.stack([np.cos(theta), np.sin(theta)], 1),
+        offsets=rng.uniform(0.3, 0.7, e) * size * (np.abs(np.cos(theta)) + np.abs(np.sin(theta))),
+        steps=rng.normal(0, 0.25, (e, 3)),
+        base=rng.uniform(0.3, 0.7, 3))
+
+
+def config5_batch(step: int, batch: int = 16, size: int = 48):
+    """(lr images [B, 3, 48, 48] float32, HR targets list of [3, floor(48 s)]^2,
+    scales) for training step `step` (seed 1000 * step + i per sample)."""
+    scales = config5_scales(10_000 + step, batch)
+    lrs, hrs = [], []
+    ys, xs = np.mgrid[0:size, 0:size]
+    for i, s in enumerate(scales):
+        f = image_function(1000 * step + i, size)
+        lrs.append(f(xs, ys).astype(np.float32))
+        n = out_size(size, s)
+        Y, X = np.mgrid[0:n, 0:n] / np.float64(np.float32(s))
+        hrs.append(f(X, Y).astype(np.float32))
+    return np.stack(lrs), hrs, scales
