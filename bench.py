@@ -39,15 +39,17 @@ UNIT = "HR Mpix/s"
 # ALU roofline of the raster kernels (derivation in the design doc). Measured on
 # GB300 with a probe: an SM issues 4 warp-instructions per clock; MUFU.EX2 runs
 # at 32 lanes/clk/SM and holds its scheduler for 4 issue cycles per warp
-# instruction; FP32 work can be packed two-wide (FFMA2/FADD2/FMUL2). Per
-# (Gaussian, pixel) pair the method needs 1 exp2 and
-#   forward: 5 FP32 ops (exponent 2, colour 3)               -> 4 + 5/2  = 6.5 cycles
-#   adjoint: 12 FP32 ops (exponent 2, g.c 3, G w Y 2, Y      -> 4 + 12/2 = 10 cycles
-#            moments 2, colour grads 3)
-# per warp of 32 pairs, so peak pairs/clk/SM = 4 * 32 / cycles.
+# instruction; the FP32 pipe does 32 lane-operations per clock per scheduler,
+# packed two-wide (FFMA2/FADD2/FMUL2) or not, so packing halves issue slots but
+# not FP32 pipe time. Per (Gaussian, pixel) pair the method needs 1 exp2 and
+#   forward: 5 FP32 ops (exponent 2, colour 3):
+#            max(FP32 pipe 5, issue 4 + 5/2)  = 6.5 cycles per warp of pairs
+#   adjoint: 12 FP32 ops (exponent 2, g.c 3, G w Y 2, Y moments 2, colour 3):
+#            max(FP32 pipe 12, issue 4 + 12/2) = 12 cycles per warp of pairs
+# so peak pairs/clk/SM = 4 * 32 / cycles.
 SMS = 152
 WARP_ISSUE_PER_SM_CLK = 4
-PAIR_CYCLES = {"raster_fwd": 6.5, "raster_bwd": 10.0}
+PAIR_CYCLES = {"raster_fwd": 6.5, "raster_bwd": 12.0}
 
 
 def load_peaks():
@@ -70,6 +72,7 @@ WORKLOADS = {
     "c4x12-f16": "LR 480x270, m=4 (N=518,400), x12 -> 5760x3240, forward + adjoint, FP16 params",
     "c4x12-f32": "LR 480x270, m=4 (N=518,400), x12 -> 5760x3240, forward + adjoint, FP32 params",
     "c3": "16 images, LR 64..480 x 64..360, m=1, s ~ U[1.5, 12], batched forward, FP32 params",
+    "c3eq": "16 equal images (config 3's mean LR size and mean scale), batched forward, FP32",
     "c5": "training step: batch 16 of 48x48 LR crops, s ~ U[1, 4], 8-block 64-ch conv encoder + "
           "1x1 Gaussian head, BF16 params, batched render fwd+bwd, L1 loss, Adam",
 }
@@ -89,6 +92,9 @@ def workload(name):
         return g, v, True, dt
     if name == "c3":
         g, v = S.config3()
+        return g, v, False, "f32"
+    if name == "c3eq":
+        g, v = S.config3_equal()
         return g, v, False, "f32"
     raise SystemExit(f"unknown workload {name}")
 
@@ -241,6 +247,23 @@ def run_gpu(args, rank, world, local_rank):
     gs.timing_enable([])
     stage = {k: round(v[0] / 3, 5) for k, v in gs.timing_read().items()}
 
+    # ---- measured unit throughputs (the ALU roofline's inputs) ----
+    unit_rates = None
+    if rank == 0 and not args.no_probe:
+        pk = gs.render.probe_peaks() if hasattr(gs, "render") and hasattr(gs.render, "probe_peaks") \
+            else None
+        if pk is None:
+            import importlib
+            pk = importlib.import_module("paper_2501_06838_gb300.render").probe_peaks()
+        f_max = float(load_peaks()[0].get("sm_max_mhz", 2070.0)) * 1e6
+        per = lambda v: round(v / pk["sm_count"] / f_max, 2)
+        unit_rates = {"ffma_per_sm_clk": per(pk["ffma_per_s"]),
+                      "ffma2_lane_ops_per_sm_clk": per(pk["ffma2_lane_ops_per_s"]),
+                      "ex2_per_sm_clk": per(pk["ex2_per_s"]),
+                      "fwd_pairs_scalar_per_sm_clk": per(pk["fwd_pairs_scalar_per_s"]),
+                      "fwd_pairs_packed_per_sm_clk": per(pk["fwd_pairs_packed_per_s"]),
+                      "clock_basis_mhz": f_max / 1e6}
+
     # ---- roofline of the dominant kernel ----
     peaks, peak_src = load_peaks()
     f_clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
@@ -256,8 +279,8 @@ def run_gpu(args, rank, world, local_rank):
                 "peak": round(peak, 2), "unit": "Gpair/s", "frac": round(achieved / peak, 4),
                 "traffic": None,
                 "peak_basis": (f"{SMS} SMs x {WARP_ISSUE_PER_SM_CLK} warp-issue/clk x 32 x "
-                               f"{f_clk / 1e6:.0f} MHz / {PAIR_CYCLES[dom]} issue cycles per warp "
-                               f"of pairs ({peak_src} sm_max_mhz)"),
+                               f"{f_clk / 1e6:.0f} MHz / {PAIR_CYCLES[dom]} cycles per warp of pairs "
+                               f"({peak_src} sm_max_mhz)"),
                 "pairs_per_launch": pairs, "ms_per_launch": round(ms / cnt, 5)}
 
     res = {
@@ -267,7 +290,7 @@ def run_gpu(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": dtname, "data": "synthetic",
         "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}",
                    "l2": "flushed before every step (256 MiB write, outside the timed events)",
-                   "tile": plan.V[0].tile or 16, "smem_batch": plan.V[0].batch or 64,
+                   "tile": plan.V[0].tile or 16, "smem_batch": plan.V[0].batch or 32,
                    "hr_pixels_per_step": hr_pix, "gaussians": sum(g.n for g in dgs),
                    "parallelism": f"replicas x{world} (one full workload per GPU)"},
         "fwd_mpix_s": round(hr_pix * args.steps / (sum(fwd_ms) * 1e-3) / 1e6, 2),
@@ -275,6 +298,7 @@ def run_gpu(args, rank, world, local_rank):
         "stage_ms_per_step": stage,
         "pairs": {"pixel_pairs": stats["pixel_pairs"], "tile_pairs": stats["tile_pairs"]},
         "roofline": roof, "gpu_launches": int(launches), "clocks": clk,
+        "unit_rates": unit_rates,
     }
 
     # ---- end to end through the public API with host buffers ----
@@ -523,6 +547,7 @@ def main():
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-probe", action="store_true", help="skip the unit-throughput probe")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-step-seconds", type=float, default=3.0)
     args = ap.parse_args()

@@ -201,6 +201,17 @@ def config3(n_images: int = 16):
     return gs, vs
 
 
+def config3_equal(n_images: int = 16):
+    """16 images of one size: the mean LR size (rounded to a multiple of 4) and
+    the mean scale of config 3; the equal-size reference for its throughput."""
+    sz = config3_sizes(0, n_images)
+    h = int(round(np.mean([a for a, _, _ in sz]) / 4)) * 4
+    w = int(round(np.mean([b for _, b, _ in sz]) / 4)) * 4
+    s = float(np.float32(np.mean([c for _, _, c in sz])))
+    gs = [draw_gaussians(200 + i, h, w, 1, (0.3, 2.0)) for i in range(n_images)]
+    return gs, [View(h, w, out_size(h, s), out_size(w, s), s) for _ in range(n_images)]
+
+
 def config4(scale: float = 12.0, dtype: str = "bf16"):
     """Reduced precision: LR 480x270 (W x H), m=4 (N=518,400), sigma in [0.2, 3]."""
     g = draw_gaussians(0, 270, 480, 4, (0.2, 3.0), dtype=dtype)

@@ -201,6 +201,23 @@ gs_status gs_timing_enable(int32_t kernel_mask);
 int32_t gs_timing_read(double* ms_out, int64_t* count_out, int32_t n);
 const char* gs_kernel_name(int32_t id);
 
+/* Measured throughputs of the units that bound the raster kernels. */
+typedef struct gs_peaks {
+  double ffma_per_s;              /* scalar FP32 FMA lane-operations per second */
+  double ffma2_lane_ops_per_s;    /* FP32 FMA lane-operations per second, packed two-wide */
+  double ex2_per_s;               /* MUFU.EX2 lane-operations per second */
+  double fwd_pairs_scalar_per_s;  /* forward (Gaussian, pixel) pair mix, scalar FP32 */
+  double fwd_pairs_packed_per_s;  /* the same mix in packed FP32x2 */
+  int32_t sm_count;
+  int32_t reserved;
+} gs_peaks;
+
+/* Runs five short throughput kernels on the current device (about 50 ms in
+ * total) and fills *out (host). scratch: device buffer of at least
+ * 6 * SM count * 256 floats, used only to keep results alive. Synchronous.
+ * Not part of the method: it supplies the ALU roofline's denominators. */
+gs_status gs_probe_peaks(void* scratch, size_t scratch_bytes, void* stream, gs_peaks* out);
+
 /* Library build identity, e.g. "gs 0.1 sm_103a". */
 const char* gs_version(void);
 

@@ -21,7 +21,8 @@ GS_NORM_DENSITY, GS_NORM_PEAK = 0, 1
 EXPORTS = ("gs_workspace_size", "gs_count_pairs", "gs_render_fwd", "gs_render_bwd",
            "gs_render_batched", "gs_render_batched_bwd", "gs_sync_status", "gs_read_stats",
            "gs_last_error", "gs_status_string", "gs_launch_count", "gs_timing_enable",
-           "gs_timing_read", "gs_kernel_name", "gs_version", "gs_render_fwd_noalloc")
+           "gs_timing_read", "gs_kernel_name", "gs_version", "gs_render_fwd_noalloc",
+           "gs_probe_peaks")
 
 
 class GsGaussians(ctypes.Structure):
@@ -43,6 +44,13 @@ class GsStats(ctypes.Structure):
     _fields_ = [("tile_pairs", ctypes.c_int64), ("pixel_pairs", ctypes.c_int64),
                 ("capacity", ctypes.c_int64), ("n_gaussians", ctypes.c_int64),
                 ("n_tiles", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+
+class GsPeaks(ctypes.Structure):
+    _fields_ = [("ffma_per_s", ctypes.c_double), ("ffma2_lane_ops_per_s", ctypes.c_double),
+                ("ex2_per_s", ctypes.c_double), ("fwd_pairs_scalar_per_s", ctypes.c_double),
+                ("fwd_pairs_packed_per_s", ctypes.c_double), ("sm_count", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class GsError(RuntimeError):
@@ -89,6 +97,7 @@ def load(path: str | None = None):
             "gs_kernel_name": (ctypes.c_char_p, [i32]),
             "gs_version": (ctypes.c_char_p, []),
             "gs_render_fwd_noalloc": (i32, [G, V, vp, vp]),
+            "gs_probe_peaks": (i32, [vp, sz, vp, ctypes.POINTER(GsPeaks)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)

@@ -84,7 +84,7 @@ Layout make_layout(int n_images, int64_t n, int64_t tiles, int64_t capacity) {
   L.capacity = capacity;
   L.tiles = (int)tiles;
   L.sort_blocks = sort_blocks_needed(capacity);
-  const int64_t hist_n = 256LL * L.sort_blocks;
+  const int64_t hist_n = 512LL * L.sort_blocks;   // up to 9-bit digits
   L.scan_parts = scan_parts_needed(n) + 1;
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
@@ -99,7 +99,7 @@ Layout make_layout(int n_images, int64_t n, int64_t tiles, int64_t capacity) {
   L.keys1 = take(4 * (size_t)capacity);
   L.vals1 = take(4 * (size_t)capacity);
   L.hist = take(4 * (size_t)hist_n);
-  L.hscan = take(4 * 256);
+  L.hscan = take(4 * 512);
   L.ranges = take(8 * (size_t)tiles);
   L.grec = take(48 * (size_t)n);
   L.total = o;
@@ -174,11 +174,14 @@ int64_t capacity_for(const Problem& P, size_t bytes) {
   return lo;
 }
 
-int radix_passes(int64_t tiles) {
+// Significant bits of the largest tile key, and the radix passes that sort them
+// (at most 9 bits per pass, as launch_sort does).
+int key_bits(int64_t tiles) {
   int bits = 0;
   while (bits < 32 && ((tiles - 1) >> bits) > 0) ++bits;
-  return (bits + 7) / 8;
+  return bits;
 }
+int radix_passes(int64_t tiles) { return (key_bits(tiles) + 8) / 9; }
 
 struct Call {
   Problem P;
@@ -291,7 +294,7 @@ gs_status run_forward(int32_t n_images, const gs_gaussians* g, const gs_view* v,
     if (e != cudaSuccess) return cuda_fail(e, "emit");
   }
   int fb = 0;
-  e = launch_sort(c.w, c.passes, s, &fb);
+  e = launch_sort(c.w, key_bits(c.P.tiles), s, &fb);
   if (e != cudaSuccess) return cuda_fail(e, "sort");
   e = launch_ranges(c.w, c.w.keys[fb], s);
   if (e != cudaSuccess) return cuda_fail(e, "ranges");

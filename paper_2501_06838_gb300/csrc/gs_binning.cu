@@ -17,9 +17,8 @@ constexpr int kTopThreads = 1024;
 
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortItems = 16;                           // per thread
-constexpr int kSortBlock = kSortThreads * kSortItems;    // 4096 pairs per block
-constexpr int kRadix = 256;
+constexpr int kSortItems = 8;                            // per thread
+constexpr int kSortBlock = kSortThreads * kSortItems;    // 2048 pairs per block
 
 // Exclusive scan of the block partials in place (one block). In count mode the
 // total is the pair count P: it is stored and checked against the capacity.
@@ -77,20 +76,27 @@ __global__ void __launch_bounds__(kFootprintBlock) k_emit(Ws w) {
   }
 }
 
+template <int BITS>
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* keys, const Header* hdr,
                                                              int shift, uint32_t* hist, int nblk) {
-  __shared__ uint32_t h[kSortWarps][kRadix];
-  for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) (&h[0][0])[i] = 0u;
+  constexpr int R = 1 << BITS;
+  __shared__ uint32_t h[kSortWarps][R];
+  for (int i = threadIdx.x; i < kSortWarps * R; i += kSortThreads) (&h[0][0])[i] = 0u;
   __syncthreads();
   const unsigned long long P = effective_pairs(hdr);
   const int64_t base = blockIdx.x * (int64_t)kSortBlock;
   const int warp = threadIdx.x >> 5;
-  for (int k = 0; k < kSortItems; ++k) {
+  uint32_t kk[kSortItems];
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {   // all loads in flight before any atomic
     const int64_t i = base + k * kSortThreads + threadIdx.x;
-    if ((unsigned long long)i < P) atomicAdd(&h[warp][(keys[i] >> shift) & (kRadix - 1)], 1u);
+    kk[k] = (unsigned long long)i < P ? __ldg(keys + i) : 0xffffffffu;
   }
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k)
+    if (kk[k] != 0xffffffffu) atomicAdd(&h[warp][(kk[k] >> shift) & (R - 1)], 1u);
   __syncthreads();
-  for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
+  for (int d = threadIdx.x; d < R; d += kSortThreads) {
     uint32_t s = 0u;
     for (int q = 0; q < kSortWarps; ++q) s += h[q][d];
     hist[(int64_t)d * nblk + blockIdx.x] = s;
@@ -117,70 +123,125 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_rowscan(uint32_t* hist, 
 }
 
 // Stable scatter of one radix pass. Warp q of block b owns the contiguous
-// chunk [b*4096 + q*512, +512) and walks it 32 pairs at a time; a pair's rank
+// chunk [b*2048 + q*256, +256) and walks it 32 pairs at a time; a pair's rank
 // among equal digits is (pairs of that digit earlier in the warp's chunk) +
-// (lower lanes with that digit in the same step). Blocks then warps then lanes
-// follow input order, which makes the pass stable.
+// (lower lanes with that digit in the same step). Blocks, then warps, then
+// lanes follow input order, which makes the pass stable. The block first
+// places its pairs in shared memory in digit order, then writes each digit's
+// run to its global position with consecutive threads on consecutive
+// addresses (coalesced stores).
+template <int BITS>
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* kin,
                                                                 const uint32_t* vin, uint32_t* kout,
                                                                 uint32_t* vout, const Header* hdr,
                                                                 int shift, const uint32_t* hist,
                                                                 const uint32_t* dtot, int nblk) {
-  __shared__ uint32_t wc[kSortWarps][kRadix];
-  __shared__ uint32_t dstart[kRadix];
+  constexpr int R = 1 << BITS;
+  constexpr int DPT = R / kSortThreads;   // digits per thread in the digit scans
+  extern __shared__ uint32_t sm[];
+  uint32_t* wc = sm;                          // [kSortWarps][R]
+  uint32_t* lstart = wc + kSortWarps * R;     // [R] block-local start of each digit
+  uint32_t* gshift = lstart + R;              // [R] global start - local start
+  uint32_t* skey = gshift + R;                // [kSortBlock]
+  uint32_t* sval = skey + kSortBlock;         // [kSortBlock]
   __shared__ unsigned long long sw[kSortThreads / 32 + 1];
-  for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) (&wc[0][0])[i] = 0u;
-  {
-    // digit start = exclusive scan of the per-digit totals
-    static_assert(kRadix == kSortThreads, "one thread per digit");
-    unsigned long long tot;
-    dstart[threadIdx.x] = (uint32_t)block_exclusive_scan<unsigned long long, kSortThreads>(
-        dtot[threadIdx.x], sw, tot);
-  }
+
+  for (int i = threadIdx.x; i < kSortWarps * R; i += kSortThreads) wc[i] = 0u;
   __syncthreads();
   const unsigned long long P = effective_pairs(hdr);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t base = blockIdx.x * (int64_t)kSortBlock + warp * (32 * kSortItems);
+  const int64_t bbase = blockIdx.x * (int64_t)kSortBlock;
+  const int64_t base = bbase + warp * (32 * kSortItems);
   const uint32_t lt_mask = (1u << lane) - 1u;
   uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
 #pragma unroll
-  for (int j = 0; j < kSortItems; ++j) {
+  for (int j = 0; j < kSortItems; ++j) {   // all loads in flight before the ranking
     const int64_t i = base + j * 32 + lane;
     const bool valid = (unsigned long long)i < P;
-    key[j] = valid ? kin[i] : 0u;
-    val[j] = valid ? vin[i] : 0u;
-    const uint32_t d = (key[j] >> shift) & (kRadix - 1);
-    uint32_t peers = __ballot_sync(0xffffffffu, valid);
+    key[j] = valid ? __ldg(kin + i) : 0u;
+    val[j] = valid ? __ldg(vin + i) : 0u;
+    rank[j] = valid ? 0u : 0xffffffffu;
+  }
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      const bool bit = (d >> b) & 1u;
-      const uint32_t bal = __ballot_sync(0xffffffffu, bit);
-      peers &= bit ? bal : ~bal;
-    }
-    const uint32_t before = valid ? wc[warp][d] : 0u;
+  for (int j = 0; j < kSortItems; ++j) {
+    const bool valid = rank[j] == 0u;
+    const uint32_t d = (key[j] >> shift) & (R - 1);
+    // lanes holding the same digit (invalid lanes match nobody)
+    const uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : (0x80000000u | lane));
+    const uint32_t before = valid ? wc[warp * R + d] : 0u;
     __syncwarp();
-    if (valid && (peers & lt_mask) == 0u) wc[warp][d] = before + __popc(peers);
+    if (valid && (peers & lt_mask) == 0u) wc[warp * R + d] = before + __popc(peers);
     __syncwarp();
     rank[j] = valid ? before + __popc(peers & lt_mask) : 0xffffffffu;
   }
   __syncthreads();
-  for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
-    uint32_t run = dstart[d] + hist[(int64_t)d * nblk + blockIdx.x];
-    for (int q = 0; q < kSortWarps; ++q) {
-      const uint32_t t = wc[q][d];
-      wc[q][d] = run;
-      run += t;
+  // block-local digit starts (exclusive scan over digits of the block counts);
+  // per-warp prefixes within each digit; global shift per digit
+  {
+    uint32_t cnt[DPT];
+    uint32_t tsum = 0u;
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+      const int d = threadIdx.x * DPT + q;
+      uint32_t c = 0u;
+      for (int w = 0; w < kSortWarps; ++w) c += wc[w * R + d];
+      cnt[q] = c;
+      tsum += c;
+    }
+    unsigned long long tot;
+    uint32_t run = (uint32_t)block_exclusive_scan<unsigned long long, kSortThreads>(tsum, sw, tot);
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+      const int d = threadIdx.x * DPT + q;
+      lstart[d] = run;
+      uint32_t wrun = run;
+      for (int w = 0; w < kSortWarps; ++w) {
+        const uint32_t t = wc[w * R + d];
+        wc[w * R + d] = wrun;
+        wrun += t;
+      }
+      run += cnt[q];
+    }
+    // global start of digit d for this block: sum of all digits < d over all
+    // blocks (exclusive scan of dtot) + this digit's count in earlier blocks
+    uint32_t dsum = 0u;
+    uint32_t dt[DPT];
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+      dt[q] = dtot[threadIdx.x * DPT + q];
+      dsum += dt[q];
+    }
+    uint32_t drun = (uint32_t)block_exclusive_scan<unsigned long long, kSortThreads>(dsum, sw, tot);
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+      const int d = threadIdx.x * DPT + q;
+      gshift[d] = drun + hist[(int64_t)d * nblk + blockIdx.x] - lstart[d];
+      drun += dt[q];
     }
   }
   __syncthreads();
 #pragma unroll
   for (int j = 0; j < kSortItems; ++j) {
     if (rank[j] == 0xffffffffu) continue;
-    const uint32_t d = (key[j] >> shift) & (kRadix - 1);
-    const uint32_t pos = wc[warp][d] + rank[j];
-    kout[pos] = key[j];
-    vout[pos] = val[j];
+    const uint32_t d = (key[j] >> shift) & (R - 1);
+    const uint32_t lp = wc[warp * R + d] + rank[j];
+    skey[lp] = key[j];
+    sval[lp] = val[j];
   }
+  __syncthreads();
+  const int nvalid = (int)min((unsigned long long)kSortBlock,
+                              P > (unsigned long long)bbase ? P - (unsigned long long)bbase : 0ull);
+  for (int i = threadIdx.x; i < nvalid; i += kSortThreads) {
+    const uint32_t k = skey[i];
+    const uint32_t pos = gshift[(k >> shift) & (R - 1)] + (uint32_t)i;
+    kout[pos] = k;
+    vout[pos] = sval[i];
+  }
+}
+
+template <int BITS>
+size_t scatter_smem() {
+  return sizeof(uint32_t) * ((size_t)(kSortWarps + 2) * (1 << BITS) + 2 * kSortBlock);
 }
 
 __global__ void __launch_bounds__(256) k_ranges(const uint32_t* keys, const Header* hdr,
@@ -214,33 +275,49 @@ cudaError_t launch_emit(const Ws& w, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_sort(const Ws& w, int passes, cudaStream_t s, int* final_buf) {
+template <int BITS>
+cudaError_t sort_pass(const Ws& w, int shift, int cur, cudaStream_t s) {
+  {
+    LaunchScope ls(kKRadixHist, s);
+    k_radix_hist<BITS><<<w.sort_blocks, kSortThreads, 0, s>>>(w.keys[cur], w.hdr, shift, w.hist,
+                                                              w.sort_blocks);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  {
+    LaunchScope ls(kKRadixRowscan, s);
+    k_radix_rowscan<<<1 << BITS, kSortThreads, 0, s>>>(w.hist, w.sort_blocks, w.hscan);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t smem = scatter_smem<BITS>();
+  static bool smem_set = false;   // opt in to > 48 KB once per process
+  if (!smem_set) {
+    e = cudaFuncSetAttribute(k_radix_scatter<BITS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    smem_set = true;
+  }
+  {
+    LaunchScope ls(kKRadixScatter, s);
+    k_radix_scatter<BITS><<<w.sort_blocks, kSortThreads, smem, s>>>(
+        w.keys[cur], w.vals[cur], w.keys[cur ^ 1], w.vals[cur ^ 1], w.hdr, shift, w.hist, w.hscan,
+        w.sort_blocks);
+  }
+  return cudaGetLastError();
+}
+
+// Stable LSD sort of the tile keys: `bits` significant bits in passes of at
+// most 9 bits (digit width ceil(bits / passes)).
+cudaError_t launch_sort(const Ws& w, int bits, cudaStream_t s, int* final_buf) {
   int cur = 0;
   *final_buf = 0;
-  if (w.sort_blocks == 0) return cudaSuccess;
+  if (w.sort_blocks == 0 || bits == 0) return cudaSuccess;
+  const int passes = (bits + 8) / 9;
+  const int width = (bits + passes - 1) / passes;   // <= 9
   for (int p = 0; p < passes; ++p) {
-    const int shift = 8 * p;
-    {
-      LaunchScope ls(kKRadixHist, s);
-      k_radix_hist<<<w.sort_blocks, kSortThreads, 0, s>>>(w.keys[cur], w.hdr, shift, w.hist,
-                                                          w.sort_blocks);
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    {
-      LaunchScope ls(kKRadixRowscan, s);
-      k_radix_rowscan<<<kRadix, kSortThreads, 0, s>>>(w.hist, w.sort_blocks, w.hscan);
-    }
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    {
-      LaunchScope ls(kKRadixScatter, s);
-      k_radix_scatter<<<w.sort_blocks, kSortThreads, 0, s>>>(w.keys[cur], w.vals[cur],
-                                                             w.keys[cur ^ 1], w.vals[cur ^ 1],
-                                                             w.hdr, shift, w.hist, w.hscan,
-                                                             w.sort_blocks);
-    }
-    e = cudaGetLastError();
+    const int shift = p * width;
+    cudaError_t e = width > 8 ? sort_pass<9>(w, shift, cur, s) : sort_pass<8>(w, shift, cur, s);
     if (e != cudaSuccess) return e;
     cur ^= 1;
   }

@@ -74,8 +74,8 @@ struct Ws {
   unsigned long long* parts;  // per-footprint-block pair counts, scanned in place
   uint32_t* keys[2];          // [capacity]
   uint32_t* vals[2];          // [capacity]
-  uint32_t* hist;             // [256][sort_blocks], row-scanned in place
-  uint32_t* hscan;            // [256] per-digit totals
+  uint32_t* hist;             // [radix][sort_blocks], row-scanned in place
+  uint32_t* hscan;            // [radix] per-digit totals
   uint2* ranges;              // [T]
   float* grec;                // [N][12] record-space gradient moments
   int64_t n;                  // total Gaussians
@@ -167,7 +167,7 @@ cudaError_t launch_preprocess(const Ws& w, cudaStream_t s);
 cudaError_t launch_preprocess_bwd(const Ws& w, cudaStream_t s);
 cudaError_t launch_scan_counts(const Ws& w, cudaStream_t s);
 cudaError_t launch_emit(const Ws& w, cudaStream_t s);
-cudaError_t launch_sort(const Ws& w, int passes, cudaStream_t s, int* final_buf);
+cudaError_t launch_sort(const Ws& w, int key_bits, cudaStream_t s, int* final_buf);
 cudaError_t launch_ranges(const Ws& w, const uint32_t* sorted_keys, cudaStream_t s);
 cudaError_t launch_raster_fwd(const Ws& w, const uint32_t* sorted_vals, int batch, cudaStream_t s);
 cudaError_t launch_raster_bwd(const Ws& w, const uint32_t* sorted_vals, int batch, cudaStream_t s);

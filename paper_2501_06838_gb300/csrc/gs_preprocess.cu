@@ -160,8 +160,9 @@ __global__ void __launch_bounds__(kFootprintBlock) k_preprocess(Ws w) {
 
 // Chain rule from the record space to the parameters. The raster adjoint left,
 // per Gaussian, the moments of Gw = (sum_k g_k c_k) 2^e over its window
-//   m = (S0, SX, SY, SXX, SXY, SYY, Cr, Cg, Cb),
-//   S_ab = sum Gw X^a Y^b, C_k = sum g_k 2^e.
+//   m = (SX, SY, SXX, SXY, SYY, Cr, Cg, Cb),
+//   S_ab = sum Gw X^a Y^b, C_k = sum g_k 2^e, and S0 = sum Gw = c . C
+// (c the record colour alpha * rgb).
 // With out_k += c_k 2^e and e = A X^2 + B X Y + C Y^2 + l (the record's
 // completed-square form expands to this):
 //   dL/dl = ln2 S0, dL/dA = ln2 SXX, dL/dB = ln2 SXY, dL/dC = ln2 SYY,
@@ -198,8 +199,10 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(Ws w) {
   const float B = q * rho * isx * isy;
   const float C = -0.5f * q * isy * isy;
   const float* m = w.grec + gi * 12;
-  const float S0 = m[0], SX = m[1], SY = m[2], SXX = m[3], SXY = m[4], SYY = m[5];
-  const float Cr = m[6], Cg = m[7], Cb = m[8];
+  const float SX = m[0], SY = m[1], SXX = m[2], SXY = m[3], SYY = m[4];
+  const float Cr = m[5], Cg = m[6], Cb = m[7];
+  const float4 rc = rec[2];
+  const float S0 = fmaf(rc.z, Cb, fmaf(rc.y, Cg, rc.x * Cr));
 
   const float dcx = -kLn2 * (2.0f * A * SX + B * SY);
   const float dcy = -kLn2 * (B * SX + 2.0f * C * SY);

@@ -79,10 +79,13 @@ __device__ __forceinline__ void load_ids(const uint32_t* vals, int bs, int nb, u
 }
 
 // Stage 1 from the raw records:
-//   gA = (cxl, sA, lx0, lx1)   gB = (cyl, sK, g, l)   gC = (r, g, b, ly0 | ly1 << 16)
-template <int TILE, int NT>
+//   gA = (cxl, sA, lx0, lx1)   gB = (cyl, sK, g, l)
+//   forward: gC = (r, g, b, ly0 | ly1 << 16)
+//   adjoint: gC = (r, r, g, g), gD = (b, b, cyl, ly0 | ly1 << 16) (colours
+//            duplicated so that they are ready-made FP32x2 operands).
+template <int TILE, int NT, bool DUP>
 __device__ __forceinline__ void stage_records(const float4* raw, int nb, int ox, int oy,
-                                              float4* gA, float4* gB, float4* gC) {
+                                              float4* gA, float4* gB, float4* gC, float4* gD) {
   for (int i = threadIdx.x; i < nb; i += NT) {
     const float4 f0 = raw[i * kRecordF4], f1 = raw[i * kRecordF4 + 1];
     const float4 f2 = raw[i * kRecordF4 + 2], f3 = raw[i * kRecordF4 + 3];
@@ -92,20 +95,27 @@ __device__ __forceinline__ void stage_records(const float4* raw, int nb, int ox,
     const int ly0 = max(__float_as_int(f3.z) - oy, 0), ly1 = min(__float_as_int(f3.w) - oy, TILE - 1);
     gA[i] = make_float4(cxl, f1.x, (float)lx0, (float)lx1);
     gB[i] = make_float4(cyl, f1.y, f1.z, f1.w);
-    gC[i] = make_float4(f2.x, f2.y, f2.z, __int_as_float(ly0 | (ly1 << 16)));
+    const float pk = __int_as_float(ly0 | (ly1 << 16));
+    if (DUP) {
+      gC[i] = make_float4(f2.x, f2.x, f2.y, f2.y);
+      gD[i] = make_float4(f2.z, f2.z, cyl, pk);
+    } else {
+      gC[i] = make_float4(f2.x, f2.y, f2.z, pk);
+    }
   }
 }
 
 // Stage 2: row terms of every staged Gaussian and pair of tile rows, as
-// (-K(2p), -K(2p+1), R(2p), R(2p+1)).
+// (-K(2p), -K(2p+1), R(2p), R(2p+1)); the packed window rows come from
+// gP[i].w.
 template <int TILE, int NT>
-__device__ __forceinline__ void stage_rowpairs(int nb, const float4* gB, const float4* gC,
+__device__ __forceinline__ void stage_rowpairs(int nb, const float4* gB, const float4* gP,
                                                float4* rq) {
   constexpr int HP = TILE / 2;
   for (int idx = threadIdx.x; idx < nb * HP; idx += NT) {
     const int i = idx / HP, p = idx - i * HP;
     const float4 b = gB[i];
-    const int pk = __float_as_int(gC[i].w);
+    const int pk = __float_as_int(gP[i].w);
     const int ly0 = pk & 0xffff, ly1 = pk >> 16;
     const int r0 = 2 * p, r1 = 2 * p + 1;
     const float Y0 = (float)r0 - b.x, Y1 = (float)r1 - b.x;
@@ -182,7 +192,7 @@ __global__ void __launch_bounds__(TILE * TILE / BY) k_raster_fwd(Ws w, const uin
     const int nb = min(BATCH, total - b * BATCH);
     cp_async_wait_all();
     __syncthreads();
-    stage_records<TILE, NT>(raw[b & 1], nb, ox, oy, gA, gB, gC);
+    stage_records<TILE, NT, false>(raw[b & 1], nb, ox, oy, gA, gB, gC, nullptr);
     __syncthreads();
     stage_rowpairs<TILE, NT>(nb, gB, gC, rq);
     __syncthreads();
@@ -228,23 +238,25 @@ __global__ void __launch_bounds__(TILE * TILE / BY) k_raster_fwd(Ws w, const uin
 //   SY = sum Gw Y, SYY = sum Gw Y^2, C_k = sum g_k 2^e,
 // and forms S0 = sum Gw = c . C, then (its X is fixed) SX = X S0, SXX = X SX,
 // SXY = X SY. Y = y - cy is rebuilt per pixel from the thread's first row.
-// Reduction over each warp's 32 lanes, batched over kRB Gaussians: lanes store
-// their nine values transposed in shared memory (row (g, f) holds the 32 lane
-// values, padded to 33 floats so that no two lanes read one bank), then lane j
-// sums rows j, j + 32, ... and adds each total to the Gaussian's record-space
-// accumulator: one atomic per (tile, Gaussian, value) and warp.
-constexpr int kRB = 4;            // Gaussians per reduction round
+// Eight values per Gaussian leave the tile (SX, SY, SXX, SXY, SYY, C_r, C_g,
+// C_b); S0 is linear in C (S0 = c . C) and is rebuilt from the summed C.
+// Reduction over each warp's 32 lanes, batched over kRB = 4 Gaussians (32
+// rows): lanes store their eight values transposed in shared memory (row
+// (g, f) holds the 32 lane values, padded to 33 floats so that no two lanes
+// read one bank), then lane j sums row j and adds the total to the Gaussian's
+// record-space accumulator: one atomic per (tile, Gaussian, value) and warp.
+constexpr int kNV = 8;            // values per Gaussian leaving a tile
+constexpr int kRB = 4;            // Gaussians per reduction round (kRB * kNV = 32 rows)
 constexpr int kRedRow = 33;       // padded row of 32 lane values
 
 template <int NQ>
 struct BwdOps {
-  float4 a, c, q[NQ];
-  float cy;
-  __device__ __forceinline__ void load(const float4* gA, const float4* gB, const float4* gC,
+  float4 a, c, e, q[NQ];
+  __device__ __forceinline__ void load(const float4* gA, const float4* gC, const float4* gD,
                                        const float4* rq, int i, int hp, int pair0) {
     a = gA[i];
     c = gC[i];
-    cy = gB[i].x;
+    e = gD[i];
     const float4* rr = rq + i * hp + pair0;
 #pragma unroll
     for (int j = 0; j < NQ; ++j) q[j] = rr[j];
@@ -256,13 +268,15 @@ struct BwdOps {
 // channel ch at rows (2j, 2j + 1).
 template <int NQ>
 __device__ __forceinline__ void bwd_gaussian(const float2 (&g)[NQ][3], const BwdOps<NQ>& o,
-                                             float fcol, int row0, float (&v)[9]) {
+                                             float fcol, int row0, float (&v)[kNV]) {
   const float Xr = fcol - o.a.x;
   const float Xs = (fcol < o.a.z || fcol > o.a.w) ? kInf : o.a.y * Xr;
   const float2 X2 = f2(Xs, Xs);
-  const float Y0 = (float)row0 - o.cy;
+  const float Y0 = (float)row0 - o.e.z;
   const float2 Yb = f2(Y0, Y0 + 1.0f);
-  const float2 cr = f2(o.c.x, o.c.x), cg = f2(o.c.y, o.c.y), cb = f2(o.c.z, o.c.z);
+  const float2 cr = f2(o.c.x, o.c.y), cg = f2(o.c.z, o.c.w), cb = f2(o.e.x, o.e.y);
+  // Y moments about the centre, accumulated per pixel (rebuilding them from
+  // moments in the row offset would cancel when the rows are far from cy).
   float2 SY = f2(0.f, 0.f), SYY = SY, Cr = SY, Cg = SY, Cb = SY;
 #pragma unroll
   for (int j = 0; j < NQ; ++j) {
@@ -279,26 +293,25 @@ __device__ __forceinline__ void bwd_gaussian(const float2 (&g)[NQ][3], const Bwd
     Cb = __ffma2_rn(g[j][2], wv, Cb);
   }
   const float cR = Cr.x + Cr.y, cG = Cg.x + Cg.y, cB = Cb.x + Cb.y;
-  const float S0 = fmaf(o.c.z, cB, fmaf(o.c.y, cG, o.c.x * cR));
+  const float S0 = fmaf(o.e.x, cB, fmaf(o.c.z, cG, o.c.x * cR));
   const float sy = SY.x + SY.y;
-  v[0] = S0;
-  v[1] = Xr * S0;
-  v[2] = sy;
-  v[3] = Xr * v[1];
-  v[4] = Xr * sy;
-  v[5] = SYY.x + SYY.y;
-  v[6] = cR;
-  v[7] = cG;
-  v[8] = cB;
+  v[0] = Xr * S0;
+  v[1] = sy;
+  v[2] = Xr * v[0];
+  v[3] = Xr * sy;
+  v[4] = SYY.x + SYY.y;
+  v[5] = cR;
+  v[6] = cG;
+  v[7] = cB;
 }
 
 template <int TILE, int BY, int PF>
 __global__ void __launch_bounds__(TILE * TILE / BY) k_raster_bwd(Ws w, const uint32_t* vals) {
   constexpr int NT = TILE * TILE / BY, NW = NT / 32, BATCH = NT * PF, NQ = BY / 2, HP = TILE / 2;
   __shared__ __align__(16) float4 raw[2][BATCH * kRecordF4];
-  __shared__ float4 gA[BATCH], gB[BATCH], gC[BATCH];
+  __shared__ float4 gA[BATCH], gB[BATCH], gC[BATCH], gD[BATCH];
   __shared__ float4 rq[BATCH * HP];
-  __shared__ float red[NW][kRB * 9 * kRedRow];
+  __shared__ float red[NW][kRB * kNV * kRedRow];
   __shared__ uint32_t gids[2][BATCH];
 
   const ImageDesc* D;
@@ -346,9 +359,9 @@ __global__ void __launch_bounds__(TILE * TILE / BY) k_raster_bwd(Ws w, const uin
     const int nb = min(BATCH, total - b * BATCH);
     cp_async_wait_all();
     __syncthreads();
-    stage_records<TILE, NT>(raw[b & 1], nb, ox, oy, gA, gB, gC);
+    stage_records<TILE, NT, true>(raw[b & 1], nb, ox, oy, gA, gB, gC, gD);
     __syncthreads();
-    stage_rowpairs<TILE, NT>(nb, gB, gC, rq);
+    stage_rowpairs<TILE, NT>(nb, gB, gD, rq);
     __syncthreads();
     if (b + 1 < nbat) {
 #pragma unroll
@@ -361,18 +374,17 @@ __global__ void __launch_bounds__(TILE * TILE / BY) k_raster_bwd(Ws w, const uin
     // One Gaussian: its moments, staged for the warp reduction; every kRB
     // Gaussians (and at the end of the batch) the warp reduces and adds.
     auto process = [&](const BwdOps<NQ>& o, int i) {
-      float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      const int pk = __float_as_int(o.c.w);
+      float v[kNV] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      const int pk = __float_as_int(o.e.w);
       if (NW == 1 || ((pk >> 16) >= wrow0 && (pk & 0xffff) <= wrow1))   // warp-uniform
         bwd_gaussian<NQ>(g, o, fcol, row0, v);
       const int slot = i % kRB;
 #pragma unroll
-      for (int f = 0; f < 9; ++f) wred[(slot * 9 + f) * kRedRow + lane] = v[f];
+      for (int f = 0; f < kNV; ++f) wred[(slot * kNV + f) * kRedRow + lane] = v[f];
       if (slot == kRB - 1 || i == nb - 1) {   // block-uniform
         __syncwarp();
-        const int rows_used = (slot + 1) * 9;
-        for (int rix = lane; rix < rows_used; rix += 32) {
-          const float* src = wred + rix * kRedRow;
+        if (lane < (slot + 1) * kNV) {
+          const float* src = wred + lane * kRedRow;
           float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
 #pragma unroll
           for (int l = 0; l < 32; l += 4) {
@@ -382,20 +394,20 @@ __global__ void __launch_bounds__(TILE * TILE / BY) k_raster_bwd(Ws w, const uin
             s3 += src[l + 3];
           }
           const float s = (s0 + s1) + (s2 + s3);
-          const int gi = i - slot + rix / 9;
-          if (s != 0.0f) atomicAdd(w.grec + (int64_t)bgid[gi] * 12 + (rix % 9), s);
+          const int gi = i - slot + lane / kNV;
+          if (s != 0.0f) atomicAdd(w.grec + (int64_t)bgid[gi] * 12 + (lane % kNV), s);
         }
         __syncwarp();
       }
     };
     // Two operand sets in registers: Gaussian i + 1's loads overlap i's math.
     BwdOps<NQ> A, B;
-    A.load(gA, gB, gC, rq, 0, HP, pair0);
+    A.load(gA, gC, gD, rq, 0, HP, pair0);
     for (int i = 0; i < nb; i += 2) {
-      if (i + 1 < nb) B.load(gA, gB, gC, rq, i + 1, HP, pair0);
+      if (i + 1 < nb) B.load(gA, gC, gD, rq, i + 1, HP, pair0);
       process(A, i);
       if (i + 1 >= nb) break;
-      if (i + 2 < nb) A.load(gA, gB, gC, rq, i + 2, HP, pair0);
+      if (i + 2 < nb) A.load(gA, gC, gD, rq, i + 2, HP, pair0);
       process(B, i + 1);
     }
     __syncthreads();

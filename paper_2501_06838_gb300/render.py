@@ -333,3 +333,16 @@ def timing_read() -> dict:
     cnt = (ctypes.c_int64 * 32)()
     n = lib.gs_timing_read(ms, cnt, 32)
     return {lib.gs_kernel_name(i).decode(): (ms[i], cnt[i]) for i in range(n) if cnt[i]}
+
+
+def probe_peaks() -> dict:
+    """Measured FFMA / FFMA2 / MUFU.EX2 rates and the forward pair mix (per
+    second and per SM per clock at the device's maximum clock)."""
+    lib = _abi.load()
+    dev = torch.cuda.current_device()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    buf = torch.empty(sms * 6 * 256, dtype=torch.float32, device="cuda")
+    pk = _abi.GsPeaks()
+    _abi.check(lib.gs_probe_peaks(buf.data_ptr(), buf.numel() * 4, _stream(), ctypes.byref(pk)),
+               "gs_probe_peaks")
+    return {f: getattr(pk, f) for f, _ in _abi.GsPeaks._fields_ if f != "reserved"}
