@@ -26,6 +26,10 @@ import numpy as np
 DTYPES = ("f32", "bf16", "f16")
 NORM_DENSITY = 0
 NORM_PEAK = 1
+WINDOW_SIGMA = 0   # |x - s mu| <= s k sigma (k = 3)
+WINDOW_RATIO = 1   # |x - s mu| < s r W, |y - s mu| < s r H (Algorithm 1, ratio r)
+ALIGN_EQ4 = 0      # HR pixel x samples LR x / s (Eq. 4 as printed)
+ALIGN_HALF = 1     # HR pixel x samples LR (x + 1/2) / s - 1/2
 
 
 def round_f32(x: np.ndarray) -> np.ndarray:
@@ -125,8 +129,10 @@ class View:
     out_h: int
     out_w: int
     scale: float          # a float32 value
-    trunc_k: float = 3.0  # footprint half-width in sigma; <= 0: untruncated
+    trunc_k: float = 3.0  # window parameter: k (sigma box) or r (ratio box); <= 0: untruncated
     norm: int = NORM_DENSITY
+    window: int = 0       # 0: |x - s mu| <= s k sigma; 1: |x - s mu| < s r W (Algorithm 1)
+    align: int = 0        # 0: HR pixel x samples x / s (Eq. 4); 1: (x + 1/2) / s - 1/2
 
     def __post_init__(self):
         self.scale = float(np.float32(self.scale))
@@ -216,6 +222,16 @@ def config4(scale: float = 12.0, dtype: str = "bf16"):
     """Reduced precision: LR 480x270 (W x H), m=4 (N=518,400), sigma in [0.2, 3]."""
     g = draw_gaussians(0, 270, 480, 4, (0.2, 3.0), dtype=dtype)
     return [g], [View(270, 480, out_size(270, scale), out_size(480, scale), scale)]
+
+
+def ratio_ablation(scale: float = 4.0, r: float = 0.1, hr: int = 720):
+    """The shape of the rasterization-ratio ablation (Sec. 3.1, r-ablation table):
+    a square hr x hr output from an LR image of hr / s pixels a side, m = 16
+    Gaussians per LR pixel, Algorithm 1's ratio window with ratio r."""
+    lr = int(round(hr / scale))
+    g = draw_gaussians(0, lr, lr, 16, (0.2, 3.0))
+    return [g], [View(lr, lr, out_size(lr, scale), out_size(lr, scale), scale, trunc_k=r,
+                      window=WINDOW_RATIO)]
 
 
 def config5_scales(seed: int = 0, batch: int = 16):

@@ -10,6 +10,8 @@ reproducible) and wraps it with ctypes/numpy.
 
 Functions (all citations are to GSASR, arXiv 2501.06838):
   render(g, view, mode="rect"|"allpairs")   Eq. 1-4 with the Algorithm-1 window
+                                             (sigma box or ratio box; Eq. 4 or
+                                             half-pixel alignment)
   adjoint(g, view, grad_out)                 d(sum grad_out*I)/d params, frozen windows
   complex_step(g, view, grad_out, gids)      same derivative by complex step
   rects(g, view)                             the integer windows R_i
@@ -34,7 +36,8 @@ class OView(ctypes.Structure):
     _fields_ = [("lr_h", ctypes.c_int32), ("lr_w", ctypes.c_int32),
                 ("out_h", ctypes.c_int32), ("out_w", ctypes.c_int32),
                 ("scale", ctypes.c_float), ("trunc_k", ctypes.c_float),
-                ("norm", ctypes.c_int32), ("ref_grid_m", ctypes.c_int32)]
+                ("norm", ctypes.c_int32), ("ref_grid_m", ctypes.c_int32),
+                ("window", ctypes.c_int32), ("align", ctypes.c_int32)]
 
 
 def build(force: bool = False) -> str:
@@ -94,7 +97,7 @@ def _args(g, view, ref_grid_m=None):
             _f64(g.rgb, (n, 3)), _f64(g.alpha, (n,))]
     m = g.ref_grid_m if ref_grid_m is None else ref_grid_m
     ov = OView(view.lr_h, view.lr_w, view.out_h, view.out_w, view.scale,
-               view.trunc_k, view.norm, m)
+               view.trunc_k, view.norm, m, getattr(view, "window", 0), getattr(view, "align", 0))
     return n, arrs, ov
 
 

@@ -13,10 +13,19 @@
 //   I_SR(x, y; s)  = sum_i G_i(x / s, y / s),  u = x/s - mu_x, v = y/s - mu_y
 //                                                                        (Eq. 4)
 // with the sum restricted, as in Algorithm 1, to the pixels inside a box window
-// around each Gaussian. The window is the integer pixel rectangle R_i of the
-// box |x/s - mu_x| <= k sx, |y/s - mu_y| <= k sy, whose edges are computed by a
-// fixed sequence of float32 operations (documented at `rect_f32`), so that the
-// GPU and this oracle take the same integer decision. Everything else is FP64.
+// around each Gaussian. The window is the integer pixel rectangle R_i of either
+//   the sigma box  |x - s mu_x| <= s k sx,  |y - s mu_y| <= s k sy  (k = 3), or
+//   the ratio box  |x - s mu_x| <  s r W,   |y - s mu_y| <  s r H
+// (Algorithm 1's rasterization ratio r, with W, H the LR width and height and
+// the HR coordinate compared with the HR centre), whose edges are computed by a
+// fixed sequence of float32 operations (documented at `rect_axis_f32`), so that
+// the GPU and this oracle take the same integer decision. Everything else is
+// FP64.
+//
+// Pixel alignment: Eq. 4 as printed samples LR point x / s at HR pixel x
+// (align = 0). The half-pixel reading samples (x + 1/2) / s - 1/2 (align = 1),
+// so that pixel centres, not corners, line up across scales; the HR centre of
+// a Gaussian is then s mu + (s - 1)/2.
 //
 // Centres: with a reference grid of m Gaussians per LR pixel, mu = p + o
 // (Sec. 3.2, Gaussian Primary Head), p on an equal-interval sqrt(m) x sqrt(m)
@@ -47,6 +56,8 @@ struct OView {
   float trunc_k;
   int32_t norm;       // 0 density (Eq. 2 as printed), 1 peak
   int32_t ref_grid_m; // 0 absolute centres, else Gaussians per LR pixel
+  int32_t window;     // 0 sigma box (trunc_k = k), 1 ratio box (trunc_k = r)
+  int32_t align;      // 0 x / s (Eq. 4 as printed), 1 (x + 1/2) / s - 1/2
 };
 
 struct Rect { int32_t x0, x1, y0, y1; };  // inclusive; empty when x0 > x1
@@ -73,17 +84,39 @@ void ref_pos(int64_t gid, int m, int lr_w, float* px, float* py) {
   *px = sx; *py = sy;
 }
 
-// One axis of R_i in float32, no contraction (build with -ffp-contract=off):
-//   c = s * mu;  r = (s * k) * sigma;  lo = ceil(c - r);  hi = floor(c + r);
-//   lo clamped below at 0, hi clamped above at n_out - 1.
-void rect_axis_f32(float mu, float sigma, float s, float k, int n_out, int32_t* lo_out, int32_t* hi_out) {
+// The HR centre of one axis in float32: c = s * mu, plus (s - 1)/2 with the
+// half-pixel alignment (0.5 s - 0.5 is exact in float32 for s < 2^23).
+float hr_centre_f32(float mu, float s, int align) {
   volatile float c = s * mu;
+  if (align) {
+    volatile float h = 0.5f * s - 0.5f;
+    volatile float ch = c + h;
+    return ch;
+  }
+  return c;
+}
+
+// One axis of R_i in float32, no contraction (build with -ffp-contract=off),
+// c the HR centre from hr_centre_f32:
+//   sigma box: r = (s * k) * sigma;  lo = ceil(c - r);      hi = floor(c + r)
+//   ratio box: r = (s * ratio) * L;  lo = floor(c - r) + 1; hi = ceil(c + r) - 1
+// (L the LR extent of the axis; the ratio box is open, so its integer edges
+// are the first integers strictly inside), then lo clamped below at 0, hi
+// clamped above at n_out - 1.
+void rect_axis_f32(float c, float sigma, float s, float k, int window, int lr_extent, int n_out,
+                   int32_t* lo_out, int32_t* hi_out) {
   volatile float sk = s * k;
-  volatile float r = sk * sigma;
+  volatile float r = window == 0 ? sk * sigma : sk * (float)lr_extent;
   volatile float a = c - r;
   volatile float b = c + r;
-  float lo = std::ceil((float)a);
-  float hi = std::floor((float)b);
+  float lo, hi;
+  if (window == 0) {
+    lo = std::ceil((float)a);
+    hi = std::floor((float)b);
+  } else {
+    lo = std::floor((float)a) + 1.0f;
+    hi = std::ceil((float)b) - 1.0f;
+  }
   if (!(lo >= 0.0f)) lo = 0.0f;              // also maps NaN to 0
   if (!(hi <= (float)(n_out - 1))) hi = (float)(n_out - 1);
   if (lo > (float)(n_out - 1) || hi < 0.0f || lo > hi) { *lo_out = 1; *hi_out = 0; return; }
@@ -123,23 +156,36 @@ Rect rect_of(const Params& P, const OView& V, int64_t i) {
   if (!(V.trunc_k > 0.0f)) { R.x0 = 0; R.x1 = V.out_w - 1; R.y0 = 0; R.y1 = V.out_h - 1; return R; }
   float mx, my;
   centre_f32(P, V, i, &mx, &my);
-  rect_axis_f32(mx, (float)P.sig[2 * i], V.scale, V.trunc_k, V.out_w, &R.x0, &R.x1);
-  rect_axis_f32(my, (float)P.sig[2 * i + 1], V.scale, V.trunc_k, V.out_h, &R.y0, &R.y1);
+  const float cx = hr_centre_f32(mx, V.scale, V.align), cy = hr_centre_f32(my, V.scale, V.align);
+  rect_axis_f32(cx, (float)P.sig[2 * i], V.scale, V.trunc_k, V.window, V.lr_w, V.out_w, &R.x0, &R.x1);
+  rect_axis_f32(cy, (float)P.sig[2 * i + 1], V.scale, V.trunc_k, V.window, V.lr_h, V.out_h, &R.y0,
+                &R.y1);
   return R;
 }
 
 // Membership used by the all-pairs mode: the defining inequalities in float32
-// (x >= s*mu - s*k*sigma and x <= s*mu + s*k*sigma), with no integer rectangle.
+// with no integer rectangle and no clamping,
+//   sigma box: c - s k sigma <= x <= c + s k sigma,
+//   ratio box: c - s r L < x < c + s r L.
 bool inside_f32(const Params& P, const OView& V, int64_t i, int x, int y) {
   if (!(V.trunc_k > 0.0f)) return true;
   float mx, my;
   centre_f32(P, V, i, &mx, &my);
   float s = V.scale, k = V.trunc_k;
-  volatile float cx = s * mx, cy = s * my, sk = s * k;
-  volatile float rx = sk * (float)P.sig[2 * i], ry = sk * (float)P.sig[2 * i + 1];
+  volatile float cx = hr_centre_f32(mx, s, V.align), cy = hr_centre_f32(my, s, V.align);
+  volatile float sk = s * k;
+  volatile float rx = V.window == 0 ? sk * (float)P.sig[2 * i] : sk * (float)V.lr_w;
+  volatile float ry = V.window == 0 ? sk * (float)P.sig[2 * i + 1] : sk * (float)V.lr_h;
   volatile float ax = cx - rx, bx = cx + rx, ay = cy - ry, by = cy + ry;
   float fx = (float)x, fy = (float)y;
-  return fx >= ax && fx <= bx && fy >= ay && fy <= by;
+  if (V.window == 0) return fx >= ax && fx <= bx && fy >= ay && fy <= by;
+  return fx > ax && fx < bx && fy > ay && fy < by;
+}
+
+// The LR coordinate that HR pixel x samples (Eq. 4; half-pixel reading when
+// align = 1).
+double sample_lr(int x, double s, int align) {
+  return align ? ((double)x + 0.5) / s - 0.5 : (double)x / s;
 }
 
 // The Gaussian's physical parameters as a scalar type T (double or complex).
@@ -160,10 +206,10 @@ template <class T> GaussT<T> gauss_of(const Params& P, const OView& V, int64_t i
 }
 
 // f(x/s, y/s) of Eq. 2 for one Gaussian.
-template <class T> T density(const GaussT<T>& g, double s, int norm, int x, int y) {
+template <class T> T density(const GaussT<T>& g, double s, int norm, int align, int x, int y) {
   const double kPi = 3.14159265358979323846;
-  T u = (double)x / s - g.mx;
-  T v = (double)y / s - g.my;
+  T u = sample_lr(x, s, align) - g.mx;
+  T v = sample_lr(y, s, align) - g.my;
   T D = (1.0 - g.rho) * (1.0 + g.rho);
   T q = (u * u / (g.sx * g.sx) - 2.0 * g.rho * u * v / (g.sx * g.sy) + v * v / (g.sy * g.sy)) / D;
   T Z = norm == 0 ? T(1.0) / (2.0 * kPi * g.sx * g.sy * std::sqrt(D)) : T(1.0);
@@ -194,6 +240,8 @@ bool valid_view(const OView* V) {
   if (V->out_h <= 0 || V->out_w <= 0 || V->lr_h <= 0 || V->lr_w <= 0) return false;
   if (!(V->scale > 0.0f) || !std::isfinite(V->scale)) return false;
   if (V->ref_grid_m < 0 || (V->ref_grid_m > 0 && isqrt_exact(V->ref_grid_m) < 0)) return false;
+  if (V->window != 0 && V->window != 1) return false;
+  if (V->align != 0 && V->align != 1) return false;
   return true;
 }
 
@@ -235,7 +283,7 @@ int gso_render(const double* off, const double* sig, const double* rho, const do
           for (int64_t i = 0; i < n; ++i) {
             if (!inside_f32(P, v, i, (int)x, (int)y)) continue;
             GaussT<double> g = gauss_of<double>(P, v, i);
-            double f = density(g, s, v.norm, (int)x, (int)y);
+            double f = density(g, s, v.norm, v.align, (int)x, (int)y);
             for (int k = 0; k < 3; ++k) out[(k * H + y) * W + x] += g.alpha * g.c[k] * f;
           }
     });
@@ -256,7 +304,7 @@ int gso_render(const double* off, const double* sig, const double* rho, const do
       GaussT<double> g = gauss_of<double>(P, v, i);
       for (int64_t y = ylo; y <= yhi; ++y)
         for (int64_t x = r.x0; x <= r.x1; ++x) {
-          double f = density(g, s, v.norm, (int)x, (int)y);
+          double f = density(g, s, v.norm, v.align, (int)x, (int)y);
           for (int k = 0; k < 3; ++k) out[(k * H + y) * W + x] += g.alpha * g.c[k] * f;
         }
     }
@@ -301,7 +349,8 @@ int gso_adjoint(const double* off, const double* sig, const double* rho, const d
       if (r.x0 <= r.x1 && r.y0 <= r.y1) {
         for (int64_t y = r.y0; y <= r.y1; ++y)
           for (int64_t x = r.x0; x <= r.x1; ++x) {
-            const double u = (double)x / s - g.mx, w = (double)y / s - g.my;
+            const double u = sample_lr((int)x, s, v.align) - g.mx;
+            const double w = sample_lr((int)y, s, v.align) - g.my;
             const double q = (u * u / (sx * sx) - 2.0 * rh * u * w / (sx * sy) + w * w / (sy * sy)) / D;
             const double f = Z * std::exp(-0.5 * q);
             double gk[3], G = 0.0;
@@ -365,7 +414,7 @@ int gso_complex_step(const double* off, const double* sig, const double* rho, co
       if (r.x0 <= r.x1 && r.y0 <= r.y1)
         for (int64_t y = r.y0; y <= r.y1; ++y)
           for (int64_t x = r.x0; x <= r.x1; ++x) {
-            C f = density(g, s, v.norm, (int)x, (int)y);
+            C f = density(g, s, v.norm, v.align, (int)x, (int)y);
             for (int c = 0; c < 3; ++c) L += grad_out[(c * H + y) * W + x] * (g.alpha * g.c[c] * f);
           }
       grads[9 * t + p] = L.imag() / h;
@@ -394,7 +443,7 @@ double gso_gaussian_loss(const double* off, const double* sig, const double* rho
   if (r.x0 <= r.x1 && r.y0 <= r.y1)
     for (int64_t y = r.y0; y <= r.y1; ++y)
       for (int64_t x = r.x0; x <= r.x1; ++x) {
-        double f = density(g, (double)v.scale, v.norm, (int)x, (int)y);
+        double f = density(g, (double)v.scale, v.norm, v.align, (int)x, (int)y);
         for (int c = 0; c < 3; ++c) L += grad_out[(c * H + y) * W + x] * (g.alpha * g.c[c] * f);
       }
   return L;

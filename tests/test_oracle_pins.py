@@ -366,3 +366,118 @@ def test_golden_regression():
     img = oracle.render(g, v)
     np.testing.assert_allclose(img[:, gold["probe_y"], gold["probe_x"]], np.array(gold["values"]),
                                rtol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Algorithm 1's ratio window: |x - s mu_x| < s r W, |y - s mu_y| < s r H (an
+# open box whose half-widths are a fraction r of the HR image). With rho = 0
+# the windowed sum factorises into two 1-D sums over that open interval.
+# --------------------------------------------------------------------------
+def test_ratio_window_separable():
+    rng = np.random.default_rng(15)
+    for _ in range(20):
+        s = float(np.float32(rng.uniform(1.5, 7.0)))
+        r = float(np.float32(rng.uniform(0.03, 0.12)))
+        Wl, Hl = 30, 22
+        sx, sy = rng.uniform(0.4, 2.5, 2)
+        mx, my = rng.uniform(8, 20, 1)[0], rng.uniform(6, 14, 1)[0]
+        g = one(mx, my, sx, sy, 0.0)
+        gmx, gmy = g.offset[0]
+        gsx, gsy = g.sigma[0]
+        Wo, Ho = S.out_size(Wl, s), S.out_size(Hl, s)
+        v = S.View(Hl, Wl, Ho, Wo, s, trunc_k=r, window=S.WINDOW_RATIO)
+
+        def window(mu, L, n):
+            lo, hi = s * mu - s * r * L, s * mu + s * r * L
+            assert min(abs(lo - round(lo)), abs(hi - round(hi))) > 1e-4   # no float32 tie
+            xs = np.arange(n)
+            return xs[(xs > lo) & (xs < hi)]
+
+        xs, ys = window(gmx, Wl, Wo), window(gmy, Hl, Ho)
+        fx = np.exp(-0.5 * (xs / s - gmx) ** 2 / gsx ** 2)
+        fy = np.exp(-0.5 * (ys / s - gmy) ** 2 / gsy ** 2)
+        Z = 1.0 / (2 * math.pi * gsx * gsy)
+        expect = g.alpha[0] * g.rgb[0] * Z * fx.sum() * fy.sum()
+        img = oracle.render(g, v)
+        np.testing.assert_allclose(img.sum(axis=(1, 2)), expect, rtol=1e-12)
+        mask = np.zeros((Ho, Wo), bool)
+        mask[ys[0]:ys[-1] + 1, xs[0]:xs[-1] + 1] = True
+        assert np.all(img[:, ~mask] == 0.0)
+        r4 = oracle.rects(g, v)[0]
+        assert (r4[0], r4[1], r4[2], r4[3]) == (xs[0], xs[-1], ys[0], ys[-1])
+
+
+@pytest.mark.parametrize("window,k,align", [(1, 0.05, 0), (1, 0.1, 1), (0, 3.0, 1), (1, 0.02, 1)])
+def test_flags_rect_equals_allpairs(window, k, align):
+    """Rectangle loop == all-pairs loop with the window's own float32 inequalities,
+    for the ratio window and for the half-pixel alignment."""
+    rng = np.random.default_rng(31 + int(k * 100) + align)
+    n = 150
+    H, W = 20, 26
+    g = one(rng.uniform(-2, W + 2, n), rng.uniform(-2, H + 2, n), rng.uniform(0.2, 2.5, n),
+            rng.uniform(0.2, 2.5, n), rng.uniform(-0.95, 0.95, n), rng.uniform(0, 1, (n, 3)),
+            rng.uniform(0, 1, n))
+    s = 2.7
+    v = S.View(H, W, S.out_size(H, s), S.out_size(W, s), s, trunc_k=k, window=window, align=align)
+    a = oracle.render(g, v)
+    b = oracle.render(g, v, mode="allpairs")
+    np.testing.assert_allclose(a, b, rtol=1e-13, atol=1e-15)
+
+
+# --------------------------------------------------------------------------
+# Half-pixel alignment: HR pixel x samples (x + 1/2)/s - 1/2.
+# --------------------------------------------------------------------------
+def _dyadic_set(seed, n, lo, hi, W):
+    rng = np.random.default_rng(seed)
+    d = lambda a: (a * 256).round() / 256
+    return (d(rng.uniform(lo, hi, n)), d(rng.uniform(lo, hi, n)), d(rng.uniform(0.3, 1.5, n)),
+            d(rng.uniform(0.3, 1.5, n)), rng.uniform(-0.9, 0.9, n), rng.uniform(0, 1, (n, 3)),
+            rng.uniform(0, 1, n))
+
+
+@pytest.mark.parametrize("trunc", [0.0, 3.0])
+def test_half_pixel_mirror(trunc):
+    """With W_out = s W, mirroring every Gaussian about the LR image centre
+    (mu_x -> W - 1 - mu_x, rho -> -rho) mirrors the aligned HR image exactly;
+    the literal Eq. 4 sampling does not have this symmetry for s != 1."""
+    W = H = 24
+    s = 3.0
+    mx, my, sx, sy, rho, rgb, al = _dyadic_set(8, 40, 3, 21, W)
+    for align, exact in ((S.ALIGN_HALF, True), (S.ALIGN_EQ4, False)):
+        v = S.View(H, W, int(s * H), int(s * W), s, trunc_k=trunc, align=align)
+        a = oracle.render(one(mx, my, sx, sy, rho, rgb, al), v)
+        b = oracle.render(one((W - 1) - mx, my, sx, sy, -rho, rgb, al), v)
+        if exact:
+            np.testing.assert_allclose(b, a[:, :, ::-1], rtol=1e-12, atol=1e-16)
+        else:
+            assert np.max(np.abs(b - a[:, :, ::-1])) > 1e-3 * np.max(np.abs(a))
+
+
+def test_half_pixel_odd_scale_subsampling():
+    """For odd integer s the aligned HR pixel s x + (s - 1)/2 samples LR point x,
+    so it equals pixel x of the s = 1 render (Eq. 3), windows included."""
+    W = H = 16
+    mx, my, sx, sy, rho, rgb, al = _dyadic_set(9, 60, 2, 14, W)
+    g = one(mx, my, sx, sy, rho, rgb, al)
+    base = oracle.render(g, S.View(H, W, H, W, 1.0))
+    for s in (3, 5):
+        h = (s - 1) // 2
+        up = oracle.render(g, S.View(H, W, H * s, W * s, float(s), align=S.ALIGN_HALF))
+        np.testing.assert_allclose(up[:, h::s, h::s], base, rtol=1e-13, atol=1e-15)
+    one_ = oracle.render(g, S.View(H, W, H, W, 1.0, align=S.ALIGN_HALF))
+    np.testing.assert_array_equal(one_, base)
+
+
+@pytest.mark.parametrize("window,k,align", [(1, 0.08, 0), (0, 3.0, 1), (1, 0.05, 1)])
+def test_adjoint_vs_complex_step_flags(window, k, align):
+    """The hand adjoint under the ratio window and the half-pixel sampling, against
+    complex-step derivatives of the forward with the same frozen windows."""
+    g = S.draw_gaussians(6, 14, 18, 1, (0.3, 2.0))
+    s = 2.7
+    v = S.View(14, 18, S.out_size(14, s), S.out_size(18, s), s, trunc_k=k, window=window,
+               align=align)
+    go = S.grad_out(2, v.out_h, v.out_w)
+    ids = S.sample_indices(3, g.n, 30)
+    adj = oracle.adjoint(g, v, go)[ids]
+    cs = oracle.complex_step(g, v, go, ids)
+    np.testing.assert_allclose(adj, cs, rtol=1e-10, atol=1e-12 * np.abs(cs).max())
