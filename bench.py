@@ -49,7 +49,29 @@ UNIT = "HR Mpix/s"
 # so peak pairs/clk/SM = 4 * 32 / cycles.
 SMS = 152
 WARP_ISSUE_PER_SM_CLK = 4
-PAIR_CYCLES = {"raster_fwd": 6.5, "raster_bwd": 12.0}
+PAIR_CYCLES = {"raster_fwd": 6.5, "raster_bwd": 12.0, "raster_bwd_gw": 12.0}
+
+# DRAM bytes (read + write) of one launch of the dominant kernel, from one ncu
+# capture per workload (summaries under profiles/), valid only for the raster
+# source they were taken on: reported as null once gs_raster.cu changes.
+TRAFFIC_SRC_SHA256 = "e7395e31b3ccf6c9ab848ffab6cd1e9047420d2f4233390e3e48eaf1e36993ad"
+TRAFFIC = {("c2", "raster_bwd"): (21317632 + 0, "profiles/raster_bwd_c2_1024x1024.md"),
+           ("c4x12-bf16", "raster_bwd"): (346347520 + 23542528,
+                                          "profiles/raster_bwd_c4x12_bf16_5760x3240.md")}
+
+
+def measured_traffic(workload_name, kernel, args):
+    import hashlib
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2501_06838_gb300",
+                       "csrc", "gs_raster.cu")
+    with open(src, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()
+    key = (workload_name, kernel)
+    default_flags = args.norm is None and args.align is None and args.ratio is None and \
+        not args.tile and not args.batch and getattr(args, "adjoint", None) is None
+    if sha != TRAFFIC_SRC_SHA256 or key not in TRAFFIC or not default_flags:
+        return None, None
+    return TRAFFIC[key]
 
 
 def load_peaks():
@@ -75,10 +97,14 @@ WORKLOADS = {
     "c3eq": "16 equal images (config 3's mean LR size and mean scale), batched forward, FP32",
     "c5": "training step: batch 16 of 48x48 LR crops, s ~ U[1, 4], 8-block 64-ch conv encoder + "
           "1x1 Gaussian head, BF16 params, batched render fwd+bwd, L1 loss, Adam",
+    "rab4": "r-ablation shape: LR 180x180, m=16 (N=518,400), x4 -> 720x720, Algorithm 1 ratio "
+            "window (--ratio, default 0.1), forward, FP32 params",
+    "rab8": "r-ablation shape: LR 90x90, m=16 (N=129,600), x8 -> 720x720, Algorithm 1 ratio "
+            "window (--ratio, default 0.1), forward, FP32 params",
 }
 
 
-def workload(name):
+def workload(name, args):
     """-> (list of GaussianSet, list of View, with_adjoint, dtype name)."""
     if name == "c2":
         g, v = S.config2()
@@ -96,7 +122,51 @@ def workload(name):
     if name == "c3eq":
         g, v = S.config3_equal()
         return g, v, False, "f32"
+    if name in ("rab4", "rab8"):
+        g, v = S.ratio_ablation(float(name[3:]), args.ratio if args.ratio is not None else 0.1)
+        return g, v, False, "f32"
     raise SystemExit(f"unknown workload {name}")
+
+
+# The paper's own render-only timings (its CUDA rasterizer on one A100, FP32,
+# supplementary "computational burden" table): 168 ms at x4 and 71 ms at x8 for
+# a 720x720 output, i.e. HR Mpix/s on the r-ablation shape with r = 0.1.
+PAPER_RENDER_MPIX_S = {"rab4": 720 * 720 / 0.168 / 1e6, "rab8": 720 * 720 / 0.071 / 1e6}
+
+
+def paper_ratio(args, value):
+    """value / the paper's number for exactly this workload, else None."""
+    if args.workload not in PAPER_RENDER_MPIX_S:
+        return None
+    if args.norm is not None or args.align is not None or args.ratio not in (None, 0.1):
+        return None
+    return round(value / PAPER_RENDER_MPIX_S[args.workload], 3)
+
+
+def view_desc(v):
+    win = (f"ratio r={v.trunc_k:g}" if v.window == S.WINDOW_RATIO else f"{v.trunc_k:g}-sigma box") \
+        if v.trunc_k > 0 else "untruncated"
+    return {"norm": "peak" if v.norm == S.NORM_PEAK else "density", "window": win,
+            "align": "half-pixel" if v.align == S.ALIGN_HALF else "x/s (Eq. 4)"}
+
+
+def apply_view_flags(views, args):
+    """--norm / --align / --ratio overrides of every view of a workload."""
+    out = []
+    for v in views:
+        d = dict(v.__dict__)
+        if args.norm is not None:
+            d["norm"] = {"density": S.NORM_DENSITY, "peak": S.NORM_PEAK}[args.norm]
+        if args.align is not None:
+            d["align"] = {"eq4": S.ALIGN_EQ4, "half": S.ALIGN_HALF}[args.align]
+        if args.ratio is not None:
+            d["window"], d["trunc_k"] = S.WINDOW_RATIO, args.ratio
+        d.pop("adjoint", None)
+        nv = S.View(**d)
+        if getattr(args, "adjoint", None) is not None:
+            nv.adjoint = {"auto": 0, "tile": 1, "gaussian": 2}[args.adjoint]
+        out.append(nv)
+    return out
 
 
 # --------------------------------------------------------------------------
@@ -166,7 +236,8 @@ def run_gpu(args, rank, world, local_rank):
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    gsets, views, with_adj, dtname = workload(args.workload)
+    gsets, views, with_adj, dtname = workload(args.workload, args)
+    views = apply_view_flags(views, args)
     tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[dtname]
 
     def dev_g(g):
@@ -201,7 +272,7 @@ def run_gpu(args, rank, world, local_rank):
     gs.timing_read()
 
     # ---- timed region (device-resident inputs) ----
-    timed_kernels = ["raster_fwd", "raster_bwd"] if with_adj else ["raster_fwd"]
+    timed_kernels = ["raster_fwd", "raster_bwd", "raster_bwd_gw"] if with_adj else ["raster_fwd"]
     clocks = ClockSampler(local_rank)
     clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -275,9 +346,11 @@ def run_gpu(args, rank, world, local_rank):
         pairs = stats["pixel_pairs"]
         achieved = pairs / per_launch_s / 1e9
         peak = SMS * f_clk * WARP_ISSUE_PER_SM_CLK * 32 / PAIR_CYCLES[dom] / 1e9
+        traffic, traffic_src = measured_traffic(args.workload, dom, args)
         roof = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 2),
                 "peak": round(peak, 2), "unit": "Gpair/s", "frac": round(achieved / peak, 4),
-                "traffic": None,
+                "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read + write)",
+                "traffic_source": traffic_src,
                 "peak_basis": (f"{SMS} SMs x {WARP_ISSUE_PER_SM_CLK} warp-issue/clk x 32 x "
                                f"{f_clk / 1e6:.0f} MHz / {PAIR_CYCLES[dom]} cycles per warp of pairs "
                                f"({peak_src} sm_max_mhz)"),
@@ -289,6 +362,7 @@ def run_gpu(args, rank, world, local_rank):
         "ms_per_step": round(total_ms / args.steps, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": dtname, "data": "synthetic",
         "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}",
+                   "view": view_desc(views[0]),
                    "l2": "flushed before every step (256 MiB write, outside the timed events)",
                    "tile": plan.V[0].tile or 16, "smem_batch": plan.V[0].batch or 32,
                    "hr_pixels_per_step": hr_pix, "gaussians": sum(g.n for g in dgs),
@@ -300,6 +374,12 @@ def run_gpu(args, rank, world, local_rank):
         "roofline": roof, "gpu_launches": int(launches), "clocks": clk,
         "unit_rates": unit_rates,
     }
+
+    vb = paper_ratio(args, res["value"])
+    if vb is not None:
+        res["vs_baseline"] = vb
+        res["baseline_note"] = (f"paper's render-only time on one A100, FP32 (computational-burden "
+                                f"table): {PAPER_RENDER_MPIX_S[args.workload]:.2f} HR Mpix/s")
 
     # ---- end to end through the public API with host buffers ----
     if not args.no_e2e:
@@ -451,8 +531,8 @@ def oracle_step(gsets, views, with_adj, band=None, threads=0, grad_outs=None):
 
 def sample_band(gsets, views, with_adj, budget):
     """None if one oracle step of the whole workload fits in `budget` seconds,
-    else the number of top rows per image that does (probed on 256 rows)."""
-    probe = min(256, max(v.out_h for v in views))
+    else the number of top rows per image that does (probed on 32 rows)."""
+    probe = min(32, max(v.out_h for v in views))
     t0 = time.time()
     oracle_step(gsets, views, with_adj, band=probe)
     t = time.time() - t0
@@ -511,7 +591,8 @@ def run_reference(args, rank, world):
         return None
     import oracle
     oracle.build()
-    gsets, views, with_adj, dtname = workload(args.workload)
+    gsets, views, with_adj, dtname = workload(args.workload, args)
+    views = apply_view_flags(views, args)
     band = sample_band(gsets, views, with_adj, max(1.0, args.ref_step_seconds))
     for _ in range(args.warmup):
         oracle_step(gsets, views, with_adj, band=band)
@@ -529,7 +610,8 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(tot / args.steps * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}"},
+            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}",
+                       "view": view_desc(views[0])},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample + (" (fwd + adjoint)" if with_adj else " (fwd)")},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -545,6 +627,14 @@ def main():
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--norm", choices=["density", "peak"], default=None,
+                    help="normalisation of Eq. 2 (default: the workload's, density)")
+    ap.add_argument("--align", choices=["eq4", "half"], default=None,
+                    help="pixel sampling: x/s (Eq. 4) or (x + 1/2)/s - 1/2")
+    ap.add_argument("--ratio", type=float, default=None,
+                    help="use Algorithm 1's ratio window with this r instead of the 3-sigma box")
+    ap.add_argument("--adjoint", choices=["auto", "tile", "gaussian"], default=None,
+                    help="adjoint kernel: per-tile with atomics, or one warp per Gaussian")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-probe", action="store_true", help="skip the unit-throughput probe")

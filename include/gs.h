@@ -73,6 +73,36 @@ typedef enum {
   GS_NORM_PEAK = 1      /* Z = 1: c is the colour at the centre (the "peak RGB" reading) */
 } gs_norm;
 
+/* The window R_i of Algorithm 1 over which a Gaussian is summed, as an integer
+ * pixel rectangle clamped to the image (c = the HR centre, see gs_align):
+ *   SIGMA: c - s k sigma <= x <= c + s k sigma per axis, k = trunc_k (3.0);
+ *   RATIO: c - s r L < x < c + s r L per axis, r = trunc_k, L = lr_w for x and
+ *          lr_h for y (Algorithm 1's rasterization ratio r, Sec. 3.1 "Fast
+ *          Rasterization", read with the HR coordinate compared against the HR
+ *          centre and the x half-width taken from the width).
+ * Edges are computed in float32 (round to nearest, no fused multiply-add):
+ * SIGMA lo = ceil(c - fl(fl(s k) sigma)), hi = floor(c + ...); RATIO
+ * lo = floor(c - fl(fl(s r) L)) + 1, hi = ceil(c + ...) - 1. trunc_k <= 0
+ * selects the whole image in either mode. */
+typedef enum { GS_WINDOW_SIGMA = 0, GS_WINDOW_RATIO = 1 } gs_window;
+
+/* Which LR point HR pixel x samples (Eq. 4):
+ *   EQ4:  x / s, as printed; the HR centre is c = fl(s mu);
+ *   HALF: (x + 1/2) / s - 1/2, pixel centres aligned across scales; the HR
+ *         centre is c = fl(fl(s mu) + (s/2 - 1/2)). */
+typedef enum { GS_ALIGN_EQ4 = 0, GS_ALIGN_HALF = 1 } gs_align;
+
+/* How the adjoint sums each Gaussian's record-space moments over its window:
+ *   TILE:     one CTA per screen tile, per-tile partial sums reduced across the
+ *             warp and added with atomics (summation order varies run to run);
+ *   GAUSSIAN: one warp per Gaussian over its own window, one fixed summation
+ *             order, no atomics: bitwise deterministic;
+ *   AUTO:     the library's choice (currently TILE, the faster of the two on
+ *             the measured workloads; GAUSSIAN re-reads grad_out once per
+ *             (Gaussian, pixel) pair instead of once per (tile, pixel)).
+ * Both compute the same derivative (Eq. 4 with the windows held fixed). */
+typedef enum { GS_ADJOINT_AUTO = 0, GS_ADJOINT_TILE = 1, GS_ADJOINT_GAUSSIAN = 2 } gs_adjoint;
+
 /* Physical (post-activation) parameters of n Gaussians, structure of arrays,
  * contiguous, all of element type `dtype`. Device pointers, caller-owned. */
 typedef struct gs_gaussians {
@@ -92,11 +122,14 @@ typedef struct gs_view {
   int32_t lr_h, lr_w;   /* LR grid (used by the reference grid and for validation) */
   int32_t out_h, out_w; /* HR output size, 1 <= out <= floor(s * lr) + 1 */
   float scale;          /* s > 0 */
-  float trunc_k;        /* footprint half-width in sigma (3.0); <= 0: whole image */
+  float trunc_k;        /* window parameter (gs_window): k in sigma (3.0) or the ratio r;
+                           <= 0: whole image */
   int32_t norm;         /* gs_norm */
   int32_t tile;         /* screen tile edge in HR px: 8, 16 or 32 (0 = 16) */
   int32_t batch;        /* Gaussians per shared-memory batch, 32..512 (0 = default) */
-  int32_t reserved;     /* must be 0 */
+  int32_t window;       /* gs_window */
+  int32_t align;        /* gs_align */
+  int32_t adjoint;      /* gs_adjoint; every view of one batched call must agree */
 } gs_view;
 
 /* Counters of the last forward call on a workspace. */

@@ -52,7 +52,7 @@ cudaEvent_t take_event() {
 const char* kKernelNames[kKNumKernels] = {
     "setup",      "preprocess",    "reserved",      "scan_top",   "radix_rowscan",
     "emit",       "radix_hist",    "radix_scatter", "ranges",     "raster_fwd",
-    "raster_bwd", "preprocess_bwd", "memset"};
+    "raster_bwd", "preprocess_bwd", "memset",        "raster_bwd_gw"};
 
 gs_status fail(gs_status st, const char* fmt, ...) {
   char buf[512];
@@ -115,6 +115,7 @@ struct Problem {
   int64_t n;
   int64_t tiles;
   int tile, batch;
+  int adjoint;   // gs_adjoint resolved: 1 tile, 2 Gaussian-warp
 };
 
 gs_status validate(int32_t n_images, const gs_gaussians* g, const gs_view* v, Problem* P) {
@@ -125,6 +126,7 @@ gs_status validate(int32_t n_images, const gs_gaussians* g, const gs_view* v, Pr
   P->tiles = 0;
   P->tile = tile_of(v[0]);
   P->batch = batch_of(v[0]);
+  P->adjoint = v[0].adjoint == GS_ADJOINT_GAUSSIAN ? GS_ADJOINT_GAUSSIAN : GS_ADJOINT_TILE;
   for (int i = 0; i < n_images; ++i) {
     const gs_gaussians& G = g[i];
     const gs_view& V = v[i];
@@ -139,7 +141,14 @@ gs_status validate(int32_t n_images, const gs_gaussians* g, const gs_view* v, Pr
       return fail(GS_ERR_INVALID, "image %lld: scale must be finite and > 0", (long long)i);
     if (!std::isfinite(V.trunc_k)) return fail(GS_ERR_INVALID, "image %lld: trunc_k not finite", (long long)i);
     if (V.norm != 0 && V.norm != 1) return fail(GS_ERR_INVALID, "image %lld: unknown norm", (long long)i);
-    if (V.reserved != 0) return fail(GS_ERR_INVALID, "image %lld: reserved must be 0", (long long)i);
+    if (V.window != 0 && V.window != 1)
+      return fail(GS_ERR_INVALID, "image %lld: unknown window", (long long)i);
+    if (V.align != 0 && V.align != 1) return fail(GS_ERR_INVALID, "image %lld: unknown align", (long long)i);
+    if (V.align == 1 && !(V.scale < 8388608.0f))
+      return fail(GS_ERR_INVALID, "image %lld: half-pixel alignment needs scale < 2^23", (long long)i);
+    if (V.adjoint < 0 || V.adjoint > 2) return fail(GS_ERR_INVALID, "image %lld: unknown adjoint", (long long)i);
+    if (V.adjoint != v[0].adjoint)
+      return fail(GS_ERR_INVALID, "image %lld: adjoint differs from image 0", (long long)i);
     const double sh = std::floor((double)V.scale * V.lr_h) + 1.0;
     const double sw = std::floor((double)V.scale * V.lr_w) + 1.0;
     if ((double)V.out_h > sh || (double)V.out_w > sw)
@@ -262,7 +271,9 @@ gs_status upload_images(const Call& c, const gs_gaussians* g, const gs_view* v, 
       d.out_w = v[i].out_w;
       d.scale = v[i].scale;
       d.trunc_k = v[i].trunc_k;
-      d.norm = v[i].norm;
+      d.flags = (v[i].norm == GS_NORM_PEAK ? kFlagPeak : 0) |
+                (v[i].window == GS_WINDOW_RATIO ? kFlagRatio : 0) |
+                (v[i].align == GS_ALIGN_HALF ? kFlagHalf : 0);
       d.tiles_x = (v[i].out_w + tile - 1) / tile;
       d.tiles_y = (v[i].out_h + tile - 1) / tile;
       d.t_base = tbase;
@@ -317,14 +328,21 @@ gs_status run_backward(int32_t n_images, const gs_gaussians* g, const gs_view* v
   st = upload_images(c, g, v, nullptr, grad_outs, grads, 0, s);
   if (st != GS_OK) return st;
   if (c.w.n == 0) return GS_OK;
-  {
-    LaunchScope ls(kKMemset, s);
-    cudaError_t e = cudaMemsetAsync(c.w.grec, 0, 48 * (size_t)c.w.n, s);
-    if (e != cudaSuccess) return cuda_fail(e, "memset");
+  cudaError_t e;
+  if (c.P.adjoint == GS_ADJOINT_TILE) {
+    {
+      LaunchScope ls(kKMemset, s);
+      e = cudaMemsetAsync(c.w.grec, 0, 48 * (size_t)c.w.n, s);
+      if (e != cudaSuccess) return cuda_fail(e, "memset");
+    }
+    const int fb = c.passes & 1;
+    e = launch_raster_bwd(c.w, c.w.vals[fb], c.P.batch, s);
+    if (e != cudaSuccess) return cuda_fail(e, "raster_bwd");
+  } else {
+    // one warp per Gaussian writes all its moments: no clearing, no atomics
+    e = launch_raster_bwd_gw(c.w, s);
+    if (e != cudaSuccess) return cuda_fail(e, "raster_bwd_gw");
   }
-  const int fb = c.passes & 1;
-  cudaError_t e = launch_raster_bwd(c.w, c.w.vals[fb], c.P.batch, s);
-  if (e != cudaSuccess) return cuda_fail(e, "raster_bwd");
   e = launch_preprocess_bwd(c.w, s);
   if (e != cudaSuccess) return cuda_fail(e, "preprocess_bwd");
   return GS_OK;

@@ -30,8 +30,12 @@ struct ImageDesc {
   int64_t g_base;   // first global Gaussian index of this image
   int32_t dtype, m, lr_h, lr_w, out_h, out_w;
   float scale, trunc_k;
-  int32_t norm, tiles_x, tiles_y, t_base;  // t_base: first global tile index
+  int32_t flags, tiles_x, tiles_y, t_base;  // t_base: first global tile index
 };
+// ImageDesc::flags
+constexpr int32_t kFlagPeak = 1;   // Z = 1 instead of Eq. 2's normalisation
+constexpr int32_t kFlagRatio = 2;  // Algorithm 1's ratio window instead of the k-sigma box
+constexpr int32_t kFlagHalf = 4;   // HR pixel x samples (x + 1/2)/s - 1/2
 static_assert(sizeof(ImageDesc) == 128, "ImageDesc layout");
 
 struct SetupChunk {
@@ -171,11 +175,13 @@ cudaError_t launch_sort(const Ws& w, int key_bits, cudaStream_t s, int* final_bu
 cudaError_t launch_ranges(const Ws& w, const uint32_t* sorted_keys, cudaStream_t s);
 cudaError_t launch_raster_fwd(const Ws& w, const uint32_t* sorted_vals, int batch, cudaStream_t s);
 cudaError_t launch_raster_bwd(const Ws& w, const uint32_t* sorted_vals, int batch, cudaStream_t s);
+cudaError_t launch_raster_bwd_gw(const Ws& w, cudaStream_t s);
 
 // Kernel ids for launch accounting / per-kernel timing.
 enum KernelId {
   kKSetup = 0, kKPreprocess, kKReserved2, kKScanTop, kKRadixRowscan, kKEmit, kKRadixHist,
-  kKRadixScatter, kKRanges, kKRasterFwd, kKRasterBwd, kKPreprocessBwd, kKMemset, kKNumKernels
+  kKRadixScatter, kKRanges, kKRasterFwd, kKRasterBwd, kKPreprocessBwd, kKMemset, kKRasterBwdGw,
+  kKNumKernels
 };
 
 // Launch bookkeeping implemented in gs_api.cu: every launch goes through

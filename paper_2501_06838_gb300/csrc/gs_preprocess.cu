@@ -28,16 +28,20 @@ __global__ void k_setup(SetupChunk c, Ws w) {
 }
 
 // Integer window edge on one axis, in float32 with round-to-nearest and no
-// contraction (the __f*_rn intrinsics are never fused):
-//   c = s * mu, r = (s * k) * sigma, lo = ceil(c - r), hi = floor(c + r),
-//   lo clamped to >= 0, hi to <= n_out - 1; empty -> lo = 1, hi = 0.
-__device__ __forceinline__ void window_axis(float mu, float sig, float s, float k, int n_out,
-                                            int& lo, int& hi) {
-  float c = __fmul_rn(s, mu);
+// contraction (the __f*_rn intrinsics are never fused), c the float32 HR
+// centre:
+//   k-sigma box (Algorithm 1 with a 3-sigma footprint), closed:
+//     r = (s * k) * sigma, lo = ceil(c - r), hi = floor(c + r);
+//   ratio box (Algorithm 1's rasterization ratio, extent L = lr_w or lr_h), open:
+//     r = (s * k) * L, lo = floor(c - r) + 1, hi = ceil(c + r) - 1;
+// lo clamped to >= 0, hi to <= n_out - 1; empty -> lo = 1, hi = 0.
+__device__ __forceinline__ void window_axis(float c, float sig, int lr_extent, float s, float k,
+                                            bool ratio, int n_out, int& lo, int& hi) {
   float sk = __fmul_rn(s, k);
-  float r = __fmul_rn(sk, sig);
-  float flo = ceilf(__fsub_rn(c, r));
-  float fhi = floorf(__fadd_rn(c, r));
+  float r = __fmul_rn(sk, ratio ? (float)lr_extent : sig);
+  float a = __fsub_rn(c, r), b = __fadd_rn(c, r);
+  float flo = ratio ? __fadd_rn(floorf(a), 1.0f) : ceilf(a);
+  float fhi = ratio ? __fsub_rn(ceilf(b), 1.0f) : floorf(b);
   float last = (float)(n_out - 1);
   if (!(flo >= 0.0f)) flo = 0.0f;
   if (!(fhi <= last)) fhi = last;
@@ -100,16 +104,34 @@ __global__ void __launch_bounds__(kFootprintBlock) k_preprocess(Ws w) {
     } else {
       mux = ox; muy = oy; ex = 0.0f; ey = 0.0f;
     }
-    const float cx_hi = __fmul_rn(s, mux);
-    const float cx_lo = __fadd_rn(__fmaf_rn(s, mux, -cx_hi), __fmul_rn(s, ex));
-    const float cy_hi = __fmul_rn(s, muy);
-    const float cy_lo = __fadd_rn(__fmaf_rn(s, muy, -cy_hi), __fmul_rn(s, ey));
+    float cx_hi = __fmul_rn(s, mux);
+    float cx_lo = __fadd_rn(__fmaf_rn(s, mux, -cx_hi), __fmul_rn(s, ex));
+    float cy_hi = __fmul_rn(s, muy);
+    float cy_lo = __fadd_rn(__fmaf_rn(s, muy, -cy_hi), __fmul_rn(s, ey));
+    // Half-pixel alignment: HR pixel x samples (x + 1/2)/s - 1/2, i.e. the HR
+    // centre moves by h = s/2 - 1/2 (exact in float32 for s < 2^23). The window
+    // uses fl(fl(s mu) + h); the exponent's pair absorbs h by TwoSum.
+    float wcx = cx_hi, wcy = cy_hi;
+    if (D.flags & kFlagHalf) {
+      const float h = __fsub_rn(0.5f * s, 0.5f);
+      wcx = __fadd_rn(cx_hi, h);
+      wcy = __fadd_rn(cy_hi, h);
+      float bb = __fsub_rn(wcx, cx_hi);
+      float e = __fadd_rn(__fsub_rn(cx_hi, __fsub_rn(wcx, bb)), __fsub_rn(h, bb));
+      cx_hi = wcx;
+      cx_lo = __fadd_rn(cx_lo, e);
+      bb = __fsub_rn(wcy, cy_hi);
+      e = __fadd_rn(__fsub_rn(cy_hi, __fsub_rn(wcy, bb)), __fsub_rn(h, bb));
+      cy_hi = wcy;
+      cy_lo = __fadd_rn(cy_lo, e);
+    }
 
     int x0 = 1, x1 = 0, y0 = 1, y1 = 0;
     if (ok) {
       if (D.trunc_k > 0.0f) {
-        window_axis(mux, sx, s, D.trunc_k, D.out_w, x0, x1);
-        window_axis(muy, sy, s, D.trunc_k, D.out_h, y0, y1);
+        const bool ratio = (D.flags & kFlagRatio) != 0;
+        window_axis(wcx, sx, D.lr_w, s, D.trunc_k, ratio, D.out_w, x0, x1);
+        window_axis(wcy, sy, D.lr_h, s, D.trunc_k, ratio, D.out_h, y0, y1);
       } else {
         x0 = 0; x1 = D.out_w - 1; y0 = 0; y1 = D.out_h - 1;
       }
@@ -128,7 +150,7 @@ __global__ void __launch_bounds__(kFootprintBlock) k_preprocess(Ws w) {
     const float sK = rho * r * isy;
     const float gY = -0.5f * kLog2E * isy * isy;
     // Eq. 2 normalisation 1 / (2 pi sx sy sqrt(D)), or 1 for the peak reading.
-    const float l = D.norm == 0 ? -(kLog2TwoPi + log2f(sx) + log2f(sy) + 0.5f * log2f(Dr)) : 0.0f;
+    const float l = (D.flags & kFlagPeak) == 0 ? -(kLog2TwoPi + log2f(sx) + log2f(sy) + 0.5f * log2f(Dr)) : 0.0f;
 
     float4* rec = w.records + gi * kRecordF4;
     rec[0] = make_float4(cx_hi, cx_lo, cy_hi, cy_lo);
@@ -206,7 +228,7 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(Ws w) {
 
   const float dcx = -kLn2 * (2.0f * A * SX + B * SY);
   const float dcy = -kLn2 * (B * SX + 2.0f * C * SY);
-  const float dens = D.norm == 0 ? 1.0f : 0.0f;
+  const float dens = (D.flags & kFlagPeak) == 0 ? 1.0f : 0.0f;
   const float dsx = (kLn2 * (-2.0f * A * SXX - B * SXY) - dens * S0) / sx;
   const float dsy = (kLn2 * (-2.0f * C * SYY - B * SXY) - dens * S0) / sy;
   const float two_r_over_D = 2.0f * rho / Dr;

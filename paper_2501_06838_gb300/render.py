@@ -68,12 +68,14 @@ def _struct_g(g: Gaussians) -> _abi.GsGaussians:
                             ts[3].data_ptr(), ts[4].data_ptr(), n, _DTYPES[dt], int(g.ref_grid_m))
 
 
-def _struct_v(v, tile: int = 0, batch: int = 0) -> _abi.GsView:
+def _struct_v(v, tile: int = 0, batch: int = 0, adjoint: int = 0) -> _abi.GsView:
     tile = tile or getattr(v, "tile", 0) or 0
     batch = batch or getattr(v, "batch", 0) or 0
+    adjoint = adjoint or getattr(v, "adjoint", 0) or 0
     return _abi.GsView(int(v.lr_h), int(v.lr_w), int(v.out_h), int(v.out_w), float(v.scale),
                        float(getattr(v, "trunc_k", 3.0)), int(getattr(v, "norm", 0)),
-                       int(tile), int(batch), 0)
+                       int(tile), int(batch), int(getattr(v, "window", 0)),
+                       int(getattr(v, "align", 0)), int(adjoint))
 
 
 def _arrays(gs: Sequence[Gaussians], views, tile=0, batch=0):

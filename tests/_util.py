@@ -38,7 +38,7 @@ def psnr(a, ref):
 
 def view_with(v: S.View, **kw):
     d = dict(lr_h=v.lr_h, lr_w=v.lr_w, out_h=v.out_h, out_w=v.out_w, scale=v.scale,
-             trunc_k=v.trunc_k, norm=v.norm)
+             trunc_k=v.trunc_k, norm=v.norm, window=v.window, align=v.align)
     d.update(kw)
     return S.View(**d)
 

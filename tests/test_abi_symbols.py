@@ -38,7 +38,7 @@ def test_host_only_entry_points(lib):
     assert lib.gs_version().startswith(b"gs ")
     assert lib.gs_kernel_name(9) == b"raster_fwd"
     G = (_abi.GsGaussians * 1)(_abi.GsGaussians(1, 1, 1, 1, 1, 2304, 0, 1))
-    V = (_abi.GsView * 1)(_abi.GsView(48, 48, 192, 192, 4.0, 3.0, 0, 16, 64, 0))
+    V = (_abi.GsView * 1)(_abi.GsView(48, 48, 192, 192, 4.0, 3.0, 0, 16, 64, 0, 0, 0))
     a = lib.gs_workspace_size(1, G, V, 0)
     b = lib.gs_workspace_size(1, G, V, 100000)
     assert 0 < a < b

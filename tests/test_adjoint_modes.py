@@ -1,0 +1,117 @@
+"""The two adjoint kernels against the FP64 oracle and each other.
+
+TILE sums each Gaussian's moments per screen tile and adds them with atomics;
+GAUSSIAN gives each Gaussian one warp that walks its own window (Eq. 4's sum
+over R_i) in a fixed order, so its gradients are bitwise reproducible. Both
+must meet the adjoint bar (1e-5 normwise per gradient field, FP32 parameters)
+on even and odd output widths (the GAUSSIAN walk loads column pairs as float2
+only when rows are 8-byte aligned), narrow and wide windows, and batches.
+"""
+import numpy as np
+import pytest
+
+import gs_synthetic as S
+import oracle
+from _util import absolute, device_gaussians, normwise
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+FIELDS = ("o_x", "o_y", "sigma_x", "sigma_y", "rho", "r", "g", "b", "alpha")
+TILE, GAUSSIAN = 1, 2
+
+
+def _grads(g, v, go, mode, tile=0):
+    import torch
+    import paper_2501_06838_gb300 as gs
+    v.adjoint = mode
+    dg = device_gaussians(g)
+    _, ws = gs.render(dg, v, tile=tile, check=True)
+    gr = gs.render_bwd(dg, v, torch.from_numpy(go.astype(np.float32)).cuda(), ws, tile=tile,
+                       check=True)
+    return gr.cpu().double().numpy()
+
+
+def _check(gr, ref):
+    err = normwise(gr, ref, axis=0)
+    assert np.all(err < TOL), dict(zip(FIELDS, err))
+
+
+CASES = {
+    "c1": lambda: (S.config1()[0][0], S.config1()[1][0]),
+    "ragged_odd_width": lambda: (S.draw_gaussians(3, 37, 53, 1, (0.3, 2.0)),
+                                 S.View(37, 53, S.out_size(37, 2.7), S.out_size(53, 2.7), 2.7)),
+    "grid_m4_wide": lambda: (S.draw_gaussians(8, 16, 20, 4, (0.2, 3.0)),
+                             S.View(16, 20, S.out_size(16, 9.5), S.out_size(20, 9.5), 9.5)),
+    "untruncated": lambda: (S.draw_gaussians(5, 12, 10, 1, (0.3, 2.0)),
+                            S.View(12, 10, 42, 35, 3.5, trunc_k=0.0)),
+    "ratio_window": lambda: (S.draw_gaussians(6, 20, 26, 1, (0.3, 2.0)),
+                             S.View(20, 26, 54, 70, 2.7, trunc_k=0.1, window=S.WINDOW_RATIO)),
+    "half_pixel_peak": lambda: (S.draw_gaussians(7, 18, 22, 1, (0.3, 2.0)),
+                                S.View(18, 22, 59, 72, 3.3, norm=S.NORM_PEAK, align=S.ALIGN_HALF)),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("mode", [TILE, GAUSSIAN])
+def test_modes_vs_oracle(case, mode):
+    g, v = CASES[case]()
+    go = S.grad_out(11, v.out_h, v.out_w)
+    _check(_grads(g, v, go, mode), oracle.adjoint(g, v, go))
+
+
+def test_gaussian_mode_off_image_and_tiny_windows():
+    """Absolute centres partly or wholly outside the image, sigmas down to 0.05
+    LR px (one- and two-pixel windows: the narrowest lane layouts)."""
+    rng = np.random.default_rng(19)
+    n = 600
+    mu = np.stack([rng.uniform(-6, 36, n), rng.uniform(-6, 26, n)], 1)
+    mu[:10] += 1000.0
+    g = absolute(mu, rng.uniform(0.05, 2.5, (n, 2)), rng.uniform(-0.95, 0.95, n),
+                 rng.uniform(0, 1, (n, 3)), rng.uniform(0, 1, n), 20, 30)
+    for W in (75, 76):
+        v = S.View(20, 30, 50, W, 2.5)
+        go = S.grad_out(12, v.out_h, v.out_w)
+        _check(_grads(g, v, go, GAUSSIAN), oracle.adjoint(g, v, go))
+
+
+def test_gaussian_mode_bitwise_deterministic_and_tile_close():
+    gset, views = S.config2()
+    g, v = gset[0], views[0]
+    go = S.grad_out(1, v.out_h, v.out_w)
+    a = _grads(g, v, go, GAUSSIAN)
+    b = _grads(g, v, go, GAUSSIAN)
+    assert np.array_equal(a, b)
+    t = _grads(g, v, go, TILE)
+    ref = oracle.adjoint(g, v, go)
+    _check(a, ref)
+    _check(t, ref)
+
+
+def test_gaussian_mode_batched_mixed_widths():
+    import torch
+    import paper_2501_06838_gb300 as gs
+    gsets, views = [], []
+    for i, (h, w, s) in enumerate([(20, 26, 2.7), (17, 23, 3.1), (24, 16, 1.5), (9, 31, 6.25)]):
+        gsets.append(S.draw_gaussians(60 + i, h, w, 1, (0.3, 2.0)))
+        v = S.View(h, w, S.out_size(h, s), S.out_size(w, s), s)
+        v.adjoint = GAUSSIAN
+        views.append(v)
+    dgs = [device_gaussians(g) for g in gsets]
+    outs, ws = gs.render_batched(dgs, views, check=True)
+    gos = [S.grad_out(70 + i, v.out_h, v.out_w) for i, v in enumerate(views)]
+    grads = gs.render_batched_bwd(dgs, views, [torch.from_numpy(x.astype(np.float32)).cuda()
+                                               for x in gos], ws, check=True)
+    for g, v, go, gr in zip(gsets, views, gos, grads):
+        _check(gr.cpu().double().numpy(), oracle.adjoint(g, v, go))
+
+
+def test_mixed_adjoint_modes_rejected():
+    import paper_2501_06838_gb300 as gs
+    from paper_2501_06838_gb300 import _abi
+    g = S.draw_gaussians(1, 8, 8, 1, (0.3, 2.0))
+    v1, v2 = S.View(8, 8, 16, 16, 2.0), S.View(8, 8, 16, 16, 2.0)
+    v1.adjoint, v2.adjoint = TILE, GAUSSIAN
+    dg = device_gaussians(g)
+    with pytest.raises(_abi.GsError) as e:
+        gs.render_batched([dg, dg], [v1, v2], check=True)
+    assert e.value.status == _abi.GS_ERR_INVALID
