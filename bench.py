@@ -68,7 +68,8 @@ def measured_traffic(workload_name, kernel, args):
         sha = hashlib.sha256(f.read()).hexdigest()
     key = (workload_name, kernel)
     default_flags = args.norm is None and args.align is None and args.ratio is None and \
-        not args.tile and not args.batch and getattr(args, "adjoint", None) is None
+        not args.tile and not args.batch and getattr(args, "adjoint", None) is None and \
+        getattr(args, "binning", None) is None
     if sha != TRAFFIC_SRC_SHA256 or key not in TRAFFIC or not default_flags:
         return None, None
     return TRAFFIC[key]
@@ -143,6 +144,13 @@ def paper_ratio(args, value):
     return round(value / PAPER_RENDER_MPIX_S[args.workload], 3)
 
 
+def binning_desc(code, gsets, views):
+    grid_ok = all(g.ref_grid_m > 0 for g in gsets) and \
+        all(v.out_w <= 32767 and v.out_h <= 32767 for v in views)
+    grid = code == 2 or (code == 0 and grid_ok)
+    return "grid-implicit" if grid else "sorted pairs"
+
+
 def view_desc(v):
     win = (f"ratio r={v.trunc_k:g}" if v.window == S.WINDOW_RATIO else f"{v.trunc_k:g}-sigma box") \
         if v.trunc_k > 0 else "untruncated"
@@ -162,9 +170,12 @@ def apply_view_flags(views, args):
         if args.ratio is not None:
             d["window"], d["trunc_k"] = S.WINDOW_RATIO, args.ratio
         d.pop("adjoint", None)
+        d.pop("binning", None)
         nv = S.View(**d)
         if getattr(args, "adjoint", None) is not None:
             nv.adjoint = {"auto": 0, "tile": 1, "gaussian": 2}[args.adjoint]
+        if getattr(args, "binning", None) is not None:
+            nv.binning = {"auto": 0, "sort": 1, "grid": 2}[args.binning]
         out.append(nv)
     return out
 
@@ -365,6 +376,8 @@ def run_gpu(args, rank, world, local_rank):
                    "view": view_desc(views[0]),
                    "l2": "flushed before every step (256 MiB write, outside the timed events)",
                    "tile": plan.V[0].tile or 16, "smem_batch": plan.V[0].batch or 32,
+                   "binning": binning_desc(plan.V[0].binning, gsets, views),
+                   "adjoint": "gaussian-warp" if plan.V[0].adjoint == 2 else "tile",
                    "hr_pixels_per_step": hr_pix, "gaussians": sum(g.n for g in dgs),
                    "parallelism": f"replicas x{world} (one full workload per GPU)"},
         "fwd_mpix_s": round(hr_pix * args.steps / (sum(fwd_ms) * 1e-3) / 1e6, 2),
@@ -635,6 +648,8 @@ def main():
                     help="use Algorithm 1's ratio window with this r instead of the 3-sigma box")
     ap.add_argument("--adjoint", choices=["auto", "tile", "gaussian"], default=None,
                     help="adjoint kernel: per-tile with atomics, or one warp per Gaussian")
+    ap.add_argument("--binning", choices=["auto", "sort", "grid"], default=None,
+                    help="per-tile Gaussian lists: radix-sorted pairs or grid-implicit")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-probe", action="store_true", help="skip the unit-throughput probe")

@@ -103,6 +103,22 @@ typedef enum { GS_ALIGN_EQ4 = 0, GS_ALIGN_HALF = 1 } gs_align;
  * Both compute the same derivative (Eq. 4 with the windows held fixed). */
 typedef enum { GS_ADJOINT_AUTO = 0, GS_ADJOINT_TILE = 1, GS_ADJOINT_GAUSSIAN = 2 } gs_adjoint;
 
+/* How each screen tile finds the Gaussians whose window meets it:
+ *   SORT: every (tile, Gaussian) pair is emitted, radix-sorted by tile and cut
+ *         into per-tile runs (needs pair capacity in the workspace);
+ *   GRID: grid-implicit binning. A Gaussian's centre is mu = p + o with p on
+ *         the reference grid (Sec. 3.2), so the footprint pass records how far
+ *         any window reaches past its LR cell (and counts the pairs of every
+ *         tile), and each tile enumerates the Gaussians of the LR cells within
+ *         that reach and tests their windows. No sort: the forward leaves each
+ *         tile's list in the workspace for the adjoint (one 4-byte array of
+ *         pair capacity instead of four). Needs ref_grid_m > 0 for every image
+ *         and outputs of at most 32767 px a side (GS_ERR_UNSUPPORTED otherwise);
+ *   AUTO: GRID where it applies, else SORT.
+ * Both give every tile the same Gaussians in the same (ascending id) order, so
+ * the forward is bitwise the same. */
+typedef enum { GS_BINNING_AUTO = 0, GS_BINNING_SORT = 1, GS_BINNING_GRID = 2 } gs_binning;
+
 /* Physical (post-activation) parameters of n Gaussians, structure of arrays,
  * contiguous, all of element type `dtype`. Device pointers, caller-owned. */
 typedef struct gs_gaussians {
@@ -130,6 +146,8 @@ typedef struct gs_view {
   int32_t window;       /* gs_window */
   int32_t align;        /* gs_align */
   int32_t adjoint;      /* gs_adjoint; every view of one batched call must agree */
+  int32_t binning;      /* gs_binning; every view of one batched call must agree */
+  int32_t reserved;     /* must be 0 */
 } gs_view;
 
 /* Counters of the last forward call on a workspace. */

@@ -20,6 +20,7 @@ GS_NORM_DENSITY, GS_NORM_PEAK = 0, 1
 GS_WINDOW_SIGMA, GS_WINDOW_RATIO = 0, 1
 GS_ALIGN_EQ4, GS_ALIGN_HALF = 0, 1
 GS_ADJOINT_AUTO, GS_ADJOINT_TILE, GS_ADJOINT_GAUSSIAN = 0, 1, 2
+GS_BINNING_AUTO, GS_BINNING_SORT, GS_BINNING_GRID = 0, 1, 2
 
 EXPORTS = ("gs_workspace_size", "gs_count_pairs", "gs_render_fwd", "gs_render_bwd",
            "gs_render_batched", "gs_render_batched_bwd", "gs_sync_status", "gs_read_stats",
@@ -41,7 +42,8 @@ class GsView(ctypes.Structure):
                 ("scale", ctypes.c_float), ("trunc_k", ctypes.c_float),
                 ("norm", ctypes.c_int32), ("tile", ctypes.c_int32),
                 ("batch", ctypes.c_int32), ("window", ctypes.c_int32),
-                ("align", ctypes.c_int32), ("adjoint", ctypes.c_int32)]
+                ("align", ctypes.c_int32), ("adjoint", ctypes.c_int32),
+                ("binning", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class GsStats(ctypes.Structure):

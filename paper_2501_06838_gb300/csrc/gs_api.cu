@@ -73,17 +73,19 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
   size_t hdr, images, records, trect, counts, parts, keys0, vals0, keys1, vals1, hist, hscan,
-      ranges, grec, total;
+      ranges, grec, win, ext, tcount, total;
   int64_t n, capacity;
   int tiles, sort_blocks, scan_parts;
 };
 
-Layout make_layout(int n_images, int64_t n, int64_t tiles, int64_t capacity) {
+// grid: grid-implicit binning keeps one pair array (the per-tile lists the
+// forward leaves for the adjoint) and no sort buffers.
+Layout make_layout(int n_images, int64_t n, int64_t tiles, int64_t capacity, bool grid) {
   Layout L;
   L.n = n;
   L.capacity = capacity;
   L.tiles = (int)tiles;
-  L.sort_blocks = sort_blocks_needed(capacity);
+  L.sort_blocks = grid ? 0 : sort_blocks_needed(capacity);
   const int64_t hist_n = 512LL * L.sort_blocks;   // up to 9-bit digits
   L.scan_parts = scan_parts_needed(n) + 1;
   size_t o = 0;
@@ -94,14 +96,18 @@ Layout make_layout(int n_images, int64_t n, int64_t tiles, int64_t capacity) {
   L.trect = take(16 * (size_t)n);
   L.counts = take(4 * (size_t)n);
   L.parts = take(8 * (size_t)L.scan_parts);
-  L.keys0 = take(4 * (size_t)capacity);
+  const size_t sortcap = grid ? 0 : (size_t)capacity;
+  L.keys0 = take(4 * sortcap);
   L.vals0 = take(4 * (size_t)capacity);
-  L.keys1 = take(4 * (size_t)capacity);
-  L.vals1 = take(4 * (size_t)capacity);
+  L.keys1 = take(4 * sortcap);
+  L.vals1 = take(4 * sortcap);
   L.hist = take(4 * (size_t)hist_n);
   L.hscan = take(4 * 512);
   L.ranges = take(8 * (size_t)tiles);
   L.grec = take(48 * (size_t)n);
+  L.win = take(8 * (size_t)n);
+  L.ext = take(16 * (size_t)n_images);
+  L.tcount = take(4 * (size_t)tiles);
   L.total = o;
   return L;
 }
@@ -116,6 +122,7 @@ struct Problem {
   int64_t tiles;
   int tile, batch;
   int adjoint;   // gs_adjoint resolved: 1 tile, 2 Gaussian-warp
+  int grid;      // gs_binning resolved: 1 grid-implicit, 0 sorted pair list
 };
 
 gs_status validate(int32_t n_images, const gs_gaussians* g, const gs_view* v, Problem* P) {
@@ -127,6 +134,7 @@ gs_status validate(int32_t n_images, const gs_gaussians* g, const gs_view* v, Pr
   P->tile = tile_of(v[0]);
   P->batch = batch_of(v[0]);
   P->adjoint = v[0].adjoint == GS_ADJOINT_GAUSSIAN ? GS_ADJOINT_GAUSSIAN : GS_ADJOINT_TILE;
+  bool grid_ok = true;   // every image on a reference grid, coordinates fit int16
   for (int i = 0; i < n_images; ++i) {
     const gs_gaussians& G = g[i];
     const gs_view& V = v[i];
@@ -149,6 +157,11 @@ gs_status validate(int32_t n_images, const gs_gaussians* g, const gs_view* v, Pr
     if (V.adjoint < 0 || V.adjoint > 2) return fail(GS_ERR_INVALID, "image %lld: unknown adjoint", (long long)i);
     if (V.adjoint != v[0].adjoint)
       return fail(GS_ERR_INVALID, "image %lld: adjoint differs from image 0", (long long)i);
+    if (V.binning < 0 || V.binning > 2) return fail(GS_ERR_INVALID, "image %lld: unknown binning", (long long)i);
+    if (V.reserved != 0) return fail(GS_ERR_INVALID, "image %lld: reserved must be 0", (long long)i);
+    if (V.binning != v[0].binning)
+      return fail(GS_ERR_INVALID, "image %lld: binning differs from image 0", (long long)i);
+    if (G.ref_grid_m == 0 || V.out_w > 32767 || V.out_h > 32767) grid_ok = false;
     const double sh = std::floor((double)V.scale * V.lr_h) + 1.0;
     const double sw = std::floor((double)V.scale * V.lr_w) + 1.0;
     if ((double)V.out_h > sh || (double)V.out_w > sw)
@@ -168,6 +181,11 @@ gs_status validate(int32_t n_images, const gs_gaussians* g, const gs_view* v, Pr
     return fail(GS_ERR_INVALID, "tile must be 8, 16 or 32 (got %lld)", (long long)P->tile);
   if (P->batch < 32 || P->batch > 512)
     return fail(GS_ERR_INVALID, "batch must be in [32, 512] (got %lld)", (long long)P->batch);
+  if (v[0].binning == GS_BINNING_GRID && !grid_ok)
+    return fail(GS_ERR_UNSUPPORTED,
+                "grid binning needs every image on a reference grid (ref_grid_m > 0) and outputs "
+                "of at most 32767 px a side");
+  P->grid = (v[0].binning == GS_BINNING_GRID || (v[0].binning == GS_BINNING_AUTO && grid_ok)) ? 1 : 0;
   if (P->n >= (1LL << 31)) return fail(GS_ERR_UNSUPPORTED, "more than 2^31 - 1 Gaussians");
   if (P->tiles >= (1LL << 24)) return fail(GS_ERR_UNSUPPORTED, "more than 2^24 tiles");
   return GS_OK;
@@ -175,10 +193,10 @@ gs_status validate(int32_t n_images, const gs_gaussians* g, const gs_view* v, Pr
 
 int64_t capacity_for(const Problem& P, size_t bytes) {
   int64_t lo = 0, hi = (1LL << 31) - 1;
-  if (make_layout(P.n_images, P.n, P.tiles, 0).total > bytes) return -1;
+  if (make_layout(P.n_images, P.n, P.tiles, 0, P.grid).total > bytes) return -1;
   while (lo < hi) {
     int64_t mid = lo + (hi - lo + 1) / 2;
-    if (make_layout(P.n_images, P.n, P.tiles, mid).total <= bytes) lo = mid; else hi = mid - 1;
+    if (make_layout(P.n_images, P.n, P.tiles, mid, P.grid).total <= bytes) lo = mid; else hi = mid - 1;
   }
   return lo;
 }
@@ -208,7 +226,7 @@ gs_status prepare(int32_t n_images, const gs_gaussians* g, const gs_view* v, voi
     return fail(GS_ERR_INVALID, "workspace must be 256-byte aligned");
   const int64_t cap = capacity_for(c->P, ws_bytes);
   if (cap < 0) return fail(GS_ERR_INVALID, "workspace too small (%lld bytes)", (long long)ws_bytes);
-  c->L = make_layout(n_images, c->P.n, c->P.tiles, cap);
+  c->L = make_layout(n_images, c->P.n, c->P.tiles, cap, c->P.grid);
   char* b = static_cast<char*>(ws);
   const Layout& L = c->L;
   Ws& w = c->w;
@@ -226,6 +244,11 @@ gs_status prepare(int32_t n_images, const gs_gaussians* g, const gs_view* v, voi
   w.hscan = reinterpret_cast<uint32_t*>(b + L.hscan);
   w.ranges = reinterpret_cast<uint2*>(b + L.ranges);
   w.grec = reinterpret_cast<float*>(b + L.grec);
+  w.win = reinterpret_cast<short4*>(b + L.win);
+  w.ext = reinterpret_cast<int4*>(b + L.ext);
+  w.tcount = reinterpret_cast<uint32_t*>(b + L.tcount);
+  w.grid = c->P.grid;
+  w.pad_ = 0;
   w.n = c->P.n;
   w.capacity = cap;
   w.n_images = n_images;
@@ -250,6 +273,7 @@ gs_status upload_images(const Call& c, const gs_gaussians* g, const gs_view* v, 
     ch.first = first;
     ch.count = c.P.n_images - first < kSetupChunk ? c.P.n_images - first : kSetupChunk;
     ch.reset = (reset && first == 0) ? 1 : 0;
+    ch.reset_ext = reset ? 1 : 0;
     for (int k = 0; k < ch.count; ++k) {
       const int i = first + k;
       ImageDesc& d = ch.d[k];
@@ -296,7 +320,24 @@ gs_status run_forward(int32_t n_images, const gs_gaussians* g, const gs_view* v,
     if (!outs[i]) return fail(GS_ERR_INVALID, "null output pointer for image %lld", (long long)i);
   st = upload_images(c, g, v, outs, nullptr, nullptr, 1, s);
   if (st != GS_OK) return st;
-  cudaError_t e = launch_preprocess(c.w, s);
+  cudaError_t e;
+  if (c.w.grid) {
+    // grid-implicit binning: the footprint pass counts pairs per tile (into a
+    // cleared array) and measures the reach; the raster enumerates each
+    // tile's candidates and leaves the tile's list for the adjoint (no sort)
+    e = cudaSuccess;
+    if (c.w.tiles > 0) {
+      LaunchScope ls(kKMemset, s);
+      e = cudaMemsetAsync(c.w.tcount, 0, 4 * (size_t)c.w.tiles, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "memset");
+    e = launch_preprocess(c.w, s);
+    if (e != cudaSuccess) return cuda_fail(e, "preprocess");
+    e = launch_raster_fwd(c.w, nullptr, c.P.batch, s);
+    if (e != cudaSuccess) return cuda_fail(e, "raster_fwd");
+    return GS_OK;
+  }
+  e = launch_preprocess(c.w, s);
   if (e != cudaSuccess) return cuda_fail(e, "preprocess");
   if (c.w.n > 0) {
     e = launch_scan_counts(c.w, s);
@@ -336,7 +377,7 @@ gs_status run_backward(int32_t n_images, const gs_gaussians* g, const gs_view* v
       if (e != cudaSuccess) return cuda_fail(e, "memset");
     }
     const int fb = c.passes & 1;
-    e = launch_raster_bwd(c.w, c.w.vals[fb], c.P.batch, s);
+    e = launch_raster_bwd(c.w, c.w.grid ? c.w.vals[0] : c.w.vals[fb], c.P.batch, s);
     if (e != cudaSuccess) return cuda_fail(e, "raster_bwd");
   } else {
     // one warp per Gaussian writes all its moments: no clearing, no atomics
@@ -403,7 +444,7 @@ size_t gs_workspace_size(int32_t n_images, const gs_gaussians* g, const gs_view*
     fail(GS_ERR_INVALID, "pair_capacity out of range (%lld)", (long long)pair_capacity);
     return 0;
   }
-  return make_layout(n_images, P.n, P.tiles, pair_capacity).total;
+  return make_layout(n_images, P.n, P.tiles, pair_capacity, P.grid).total;
 }
 
 gs_status gs_count_pairs(int32_t n_images, const gs_gaussians* g, const gs_view* v, void* ws,
@@ -415,6 +456,7 @@ gs_status gs_count_pairs(int32_t n_images, const gs_gaussians* g, const gs_view*
   if (st != GS_OK) return st;
   st = upload_images(c, g, v, nullptr, nullptr, nullptr, 1, s);
   if (st != GS_OK) return st;
+  c.w.grid = 0;   // the count is the same either way; take it from the scan
   cudaError_t e = launch_preprocess(c.w, s);
   if (e != cudaSuccess) return cuda_fail(e, "preprocess");
   if (c.w.n > 0) {

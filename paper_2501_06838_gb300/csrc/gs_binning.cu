@@ -7,6 +7,10 @@
 // Algorithm 1 of GSASR (arXiv 2501.06838) touches, per Gaussian, only the HR
 // pixels of its window; binning the windows to screen tiles lets each tile
 // visit only the Gaussians whose window meets it.
+//
+// Grid-implicit binning (the raster's GridSource) builds the same per-tile
+// lists without a sort when every centre sits on the reference grid
+// (mu = p + o, Sec. 3.2).
 #include "gs_internal.cuh"
 
 namespace gs {

@@ -39,7 +39,7 @@ constexpr int32_t kFlagHalf = 4;   // HR pixel x samples (x + 1/2)/s - 1/2
 static_assert(sizeof(ImageDesc) == 128, "ImageDesc layout");
 
 struct SetupChunk {
-  int32_t first, count, reset, pad;
+  int32_t first, count, reset, reset_ext;   // reset: header (first chunk); reset_ext: reaches
   ImageDesc d[kSetupChunk];
 };
 
@@ -52,7 +52,8 @@ struct Header {
   unsigned long long capacity;
   uint32_t work_counter;
   uint32_t pad1;
-  unsigned long long reserved[11];
+  unsigned long long list_cursor;  // grid mode: pair-list slots handed out to tiles
+  unsigned long long reserved[10];
 };
 static_assert(sizeof(Header) == 128, "Header layout");
 
@@ -82,6 +83,9 @@ struct Ws {
   uint32_t* hscan;            // [radix] per-digit totals
   uint2* ranges;              // [T]
   float* grec;                // [N][12] record-space gradient moments
+  short4* win;                // [N] windows (x0, x1, y0, y1) for grid binning (empty: never meets a tile)
+  int4* ext;                  // [n_images] reach (DL, DR, DT, DB) of the windows past their LR cell, HR px
+  uint32_t* tcount;           // [T] grid mode: (tile, Gaussian) pairs per tile
   int64_t n;                  // total Gaussians
   int64_t capacity;           // pair capacity
   int32_t n_images;
@@ -90,6 +94,8 @@ struct Ws {
   int32_t tile_shift;
   int32_t sort_blocks;
   int32_t scan_parts;         // size of `parts`
+  int32_t grid;               // 1: grid-implicit binning (no pair list), 0: sorted pair list
+  int32_t pad_;
 };
 
 // ---------------------------------------------------------------------------

@@ -15,6 +15,7 @@ constexpr float kLog2TwoPi = 2.6514961294723187f;
 __global__ void k_setup(SetupChunk c, Ws w) {
   int t = threadIdx.x;
   if (t < c.count) w.images[c.first + t] = c.d[t];
+  if (t < c.count && c.reset_ext) w.ext[c.first + t] = make_int4(0, 0, 0, 0);
   if (c.reset && t == 0) {
     Header* h = w.hdr;
     h->status = 0u;
@@ -22,6 +23,7 @@ __global__ void k_setup(SetupChunk c, Ws w) {
     h->pixel_pairs = 0ull;
     h->capacity = (unsigned long long)w.capacity;
     h->work_counter = 0u;
+    h->list_cursor = 0ull;
     h->reserved[0] = (unsigned long long)w.n;
     h->reserved[1] = (unsigned long long)w.tiles;
   }
@@ -62,6 +64,9 @@ __global__ void __launch_bounds__(kFootprintBlock) k_preprocess(Ws w) {
   const int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   unsigned long long pix = 0ull;
   uint32_t cnt = 0u;
+  int4 reach = make_int4(0, 0, 0, 0);   // grid mode: window reach past the LR cell
+  int rim = -1;                          // image of `reach` (-1: none)
+  uint4 trk = make_uint4(0u, 0u, 0u, 0u);  // tile rectangle, for the per-tile counts
   if (gi < w.n) {
     const int im = image_of_gaussian(w.images, w.n_images, gi);
     const ImageDesc& D = w.images[im];
@@ -158,6 +163,23 @@ __global__ void __launch_bounds__(kFootprintBlock) k_preprocess(Ws w) {
     rec[2] = make_float4(al * cr, al * cg, al * cb, 0.0f);
     rec[3] = make_float4(__int_as_float(x0), __int_as_float(x1), __int_as_float(y0), __int_as_float(y1));
 
+    if (w.grid) {
+      // compact window for the tile test, and how far it reaches past the
+      // Gaussian's LR cell (i, j): DL = s j - x0, DR = x1 - s j (rows alike),
+      // rounded up, plus one pixel of margin for the float32 rounding of s j
+      const bool live = x0 <= x1 && y0 <= y1;
+      w.win[gi] = live ? make_short4((short)x0, (short)x1, (short)y0, (short)y1)
+                       : make_short4(32767, -32768, 32767, -32768);
+      if (live) {
+        const int64_t cell = li / D.m;
+        const float sj = s * (float)(cell % D.lr_w), si = s * (float)(cell / D.lr_w);
+        reach.x = max(0, (int)ceilf(sj - (float)x0) + 1);
+        reach.y = max(0, (int)ceilf((float)x1 - sj) + 1);
+        reach.z = max(0, (int)ceilf(si - (float)y0) + 1);
+        reach.w = max(0, (int)ceilf((float)y1 - si) + 1);
+        rim = im;
+      }
+    }
     uint4 tr = make_uint4(0u, 0u, 0u, 0u);
     if (x0 <= x1 && y0 <= y1) {
       const int tx0 = x0 >> w.tile_shift, tx1 = x1 >> w.tile_shift;
@@ -169,11 +191,47 @@ __global__ void __launch_bounds__(kFootprintBlock) k_preprocess(Ws w) {
     }
     w.trect[gi] = tr;
     w.counts[gi] = cnt;
+    trk = tr;
     if (!ok) atomicOr(&w.hdr->status, kStInvalid);
   }
   // warp sum of the window areas, one atomic per warp
   for (int o = 16; o > 0; o >>= 1) pix += __shfl_xor_sync(0xffffffffu, pix, o);
   if ((threadIdx.x & 31) == 0 && pix) atomicAdd(&w.hdr->pixel_pairs, pix);
+  if (w.grid) {
+    // pair count (no scan in grid mode) and the per-image reach: warp maxima
+    // when the whole warp is on one image, else one atomic per lane
+    unsigned long long c64 = cnt;
+    for (int o = 16; o > 0; o >>= 1) c64 += __shfl_xor_sync(0xffffffffu, c64, o);
+    if ((threadIdx.x & 31) == 0 && c64) atomicAdd(&w.hdr->pairs, c64);
+    // pairs per tile: each lane walks its tile rectangle; lanes on the same
+    // tile in the same step add together (one atomic per tile and step)
+    {
+      const int lane = threadIdx.x & 31;
+      int kx = 0, ky = 0;
+      for (uint32_t k = 0;; ++k) {
+        const bool act = k < cnt;
+        if (!__any_sync(0xffffffffu, act)) break;
+        const uint32_t t = act ? trk.x + (uint32_t)ky * trk.y + (uint32_t)kx : 0xffffffffu;
+        const unsigned grp = __match_any_sync(0xffffffffu, t);
+        if (act && (__ffs(grp) - 1) == lane) atomicAdd(w.tcount + t, (uint32_t)__popc(grp));
+        if (act && ++kx == (int)trk.z) { kx = 0; ++ky; }
+      }
+    }
+    const int im0 = __shfl_sync(0xffffffffu, rim, 0);
+    if (__all_sync(0xffffffffu, rim == im0 || rim < 0) && im0 >= 0) {
+      const int dl = __reduce_max_sync(0xffffffffu, reach.x);
+      const int dr = __reduce_max_sync(0xffffffffu, reach.y);
+      const int dt = __reduce_max_sync(0xffffffffu, reach.z);
+      const int db = __reduce_max_sync(0xffffffffu, reach.w);
+      if ((threadIdx.x & 31) == 0) {
+        int* e = reinterpret_cast<int*>(w.ext + im0);
+        atomicMax(e, dl); atomicMax(e + 1, dr); atomicMax(e + 2, dt); atomicMax(e + 3, db);
+      }
+    } else if (rim >= 0) {
+      int* e = reinterpret_cast<int*>(w.ext + rim);
+      atomicMax(e, reach.x); atomicMax(e + 1, reach.y); atomicMax(e + 2, reach.z); atomicMax(e + 3, reach.w);
+    }
+  }
   // this block's pair count, scanned over blocks by k_scan_top
   unsigned long long tot;
   block_exclusive_scan<unsigned long long, kFootprintBlock>(cnt, sw, tot);

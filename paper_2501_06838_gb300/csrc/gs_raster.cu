@@ -13,8 +13,10 @@
 //            float32 precision even at x ~ 5760) and clips its window;
 //   stage 2: per (Gaussian, pair of tile rows) the row terms of the exponent
 //              e = -(sA X - sK Y)^2 + g Y^2 + l        (log2 units)
-//            as one float4 (-K(r), -K(r+1), R(r), R(r+1)) with K = sK*Y and
-//            R = g*Y^2 + l (R = -inf outside the window rows);
+//            as one float4: (-K(r), -K(r+1), R(r), R(r+1)) for the forward
+//            and (Y(r), Y(r+1), R(r), R(r+1)) for the adjoint, which needs Y
+//            itself, with K = sK*Y and R = g*Y^2 + l (R = -inf outside the
+//            window rows);
 //   compute: per Gaussian each thread forms Xs = sA*(col - cxl) (+inf outside
 //            the window columns) and, for each of its row pairs, in packed
 //            FP32x2 arithmetic (one instruction for both rows),
@@ -26,6 +28,8 @@
 // The window masks are folded into the exponent: -inf rows and +inf columns
 // both give e = -inf and w = +0, so masked pairs cost no branch. The completed
 // square has no cancellation for any |rho| < 1 (the Y term is the marginal).
+#include <type_traits>
+
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -78,10 +82,117 @@ __device__ __forceinline__ void load_ids(const uint32_t* vals, int bs, int nb, u
   }
 }
 
+// Where a tile's Gaussian ids come from, one batch at a time (ids ascending,
+// so both sources give a tile the same Gaussians in the same order and the
+// forward the same bits).
+//
+// SortedSource: the tile's run [start, end) of the radix-sorted pair list.
+template <int NT, int PF>
+struct SortedSource {
+  const uint32_t* vals;
+  int pos, end;
+  __device__ __forceinline__ int next(uint32_t (&gid)[PF]) {
+    const int nb = max(0, min(NT * PF, end - pos));
+    load_ids<NT, PF>(vals, pos, nb, gid);
+    pos += nb;
+    return nb;
+  }
+};
+
+// GridSource (grid-implicit binning): with centres mu = p + o on the reference
+// grid, a Gaussian of LR cell (i, j) has its window within
+// [s j - DL, s j + DR] x [s i - DT, s i + DB], the per-image reach measured by
+// the footprint pass. So the tile's candidates are the Gaussians of a box of
+// LR cells: rows i0..i1, each a contiguous run of gids. Every candidate's
+// window is tested against the tile (the same test that puts a pair into the
+// sorted list); the survivors go through a shared-memory queue in gid order.
+// All warps run the enumeration (the same loads and ballots); warp 0 writes.
+template <int NT, int PF>
+struct GridSource {
+  static constexpr int BATCH = NT * PF;
+  static constexpr int KR = 4;                          // candidates per lane per round
+  static constexpr int QCAP = BATCH + 32 * KR <= 256 ? 256 : 512;
+  const short4* win;
+  uint32_t* q;           // shared [QCAP]
+  int64_t rb0, rstride;  // gid of the first candidate of row r: rb0 + r * rstride
+  int L, total, cur;     // candidates per row, in all, next to test
+  int head, tail;        // queue positions (monotonic)
+  int X0, X1, Y0, Y1;    // tile pixel bounds
+
+  __device__ __forceinline__ void sync() {
+    if (NT == 32) __syncwarp(); else __syncthreads();
+  }
+  float invL;            // 1 / L, for the row of a candidate index
+  __device__ __forceinline__ uint32_t gid_of(int c) const {
+    // r = c / L by a float reciprocal, corrected to the exact quotient
+    int r = __float2int_rz(__fmul_rn((float)c + 0.5f, invL));
+    r -= (r * L > c) ? 1 : 0;
+    r += ((r + 1) * L <= c) ? 1 : 0;
+    return (uint32_t)(rb0 + (int64_t)r * rstride + (c - r * L));
+  }
+  __device__ __forceinline__ int next(uint32_t (&gid)[PF]) {
+    const int lane = threadIdx.x & 31;
+    while (tail - head < BATCH && cur < total) {   // uniform over the CTA
+      // KR independent window loads per lane, then the ballots in candidate order
+      uint32_t g[KR];
+      short4 v[KR];
+#pragma unroll
+      for (int k = 0; k < KR; ++k) {
+        const int c = cur + 32 * k + lane;
+        g[k] = c < total ? gid_of(c) : 0u;
+        v[k] = c < total ? win[g[k]] : make_short4(32767, -32768, 32767, -32768);
+      }
+#pragma unroll
+      for (int k = 0; k < KR; ++k) {
+        const bool hit = v[k].x <= X1 && v[k].y >= X0 && v[k].z <= Y1 && v[k].w >= Y0;
+        const unsigned bal = __ballot_sync(0xffffffffu, hit);
+        if (threadIdx.x < 32 && hit)
+          q[(tail + __popc(bal & ((1u << lane) - 1u))) & (QCAP - 1)] = g[k];
+        tail += __popc(bal);
+      }
+      cur += 32 * KR;
+    }
+    sync();
+    const int nb = min(BATCH, tail - head);
+#pragma unroll
+    for (int j = 0; j < PF; ++j) {
+      const int i = j * NT + threadIdx.x;
+      gid[j] = i < nb ? q[(head + i) & (QCAP - 1)] : 0u;
+    }
+    head += nb;
+    return nb;
+  }
+};
+
+// Candidate box of a tile in grid mode (see GridSource).
+template <int TILE, int NT, int PF>
+__device__ __forceinline__ void grid_source_init(const Ws& w, const ImageDesc* D, int ox, int oy,
+                                                 uint32_t* q, GridSource<NT, PF>& g) {
+  const int4 e = w.ext[D - w.images];   // (DL, DR, DT, DB), HR px
+  const float s = D->scale;
+  g.win = w.win;
+  g.q = q;
+  g.X0 = ox; g.X1 = ox + TILE - 1; g.Y0 = oy; g.Y1 = oy + TILE - 1;
+  // A Gaussian of column j meets the tile only if s j - DL < x0 <= X1 and
+  // s j + DR > x1 >= X0; the reach carries a pixel of margin, far more than the
+  // float32 rounding of these quotients, so floor/ceil bound the cells exactly.
+  const int j0 = max(0, (int)ceilf(__fdiv_rn((float)(g.X0 - e.y), s)));
+  const int j1 = min(D->lr_w - 1, (int)floorf(__fdiv_rn((float)(g.X1 + e.x), s)));
+  const int i0 = max(0, (int)ceilf(__fdiv_rn((float)(g.Y0 - e.w), s)));
+  const int i1 = min(D->lr_h - 1, (int)floorf(__fdiv_rn((float)(g.Y1 + e.z), s)));
+  g.rstride = (int64_t)D->lr_w * D->m;
+  g.rb0 = D->g_base + ((int64_t)i0 * D->lr_w + j0) * D->m;
+  g.L = (j1 - j0 + 1) * D->m;
+  g.invL = g.L > 0 ? __frcp_rn((float)g.L) : 0.0f;
+  g.total = (j0 <= j1 && i0 <= i1) ? (i1 - i0 + 1) * g.L : 0;
+  g.cur = 0;
+  g.head = g.tail = 0;
+}
+
 // Stage 1 from the raw records:
 //   gA = (cxl, sA, lx0, lx1)   gB = (cyl, sK, g, l)
 //   forward: gC = (r, g, b, ly0 | ly1 << 16)
-//   adjoint: gC = (r, r, g, g), gD = (b, b, cyl, ly0 | ly1 << 16) (colours
+//   adjoint: gC = (r, r, g, g), gD = (b, b, -sK, ly0 | ly1 << 16) (colours
 //            duplicated so that they are ready-made FP32x2 operands).
 template <int TILE, int NT, bool DUP>
 __device__ __forceinline__ void stage_records(const float4* raw, int nb, int ox, int oy,
@@ -98,7 +209,7 @@ __device__ __forceinline__ void stage_records(const float4* raw, int nb, int ox,
     const float pk = __int_as_float(ly0 | (ly1 << 16));
     if (DUP) {
       gC[i] = make_float4(f2.x, f2.x, f2.y, f2.y);
-      gD[i] = make_float4(f2.z, f2.z, cyl, pk);
+      gD[i] = make_float4(f2.z, f2.z, -f1.y, pk);
     } else {
       gC[i] = make_float4(f2.x, f2.y, f2.z, pk);
     }
@@ -106,9 +217,9 @@ __device__ __forceinline__ void stage_records(const float4* raw, int nb, int ox,
 }
 
 // Stage 2: row terms of every staged Gaussian and pair of tile rows, as
-// (-K(2p), -K(2p+1), R(2p), R(2p+1)); the packed window rows come from
-// gP[i].w.
-template <int TILE, int NT>
+// (-K(2p), -K(2p+1), R(2p), R(2p+1)) or, with YT, (Y(2p), Y(2p+1), R(2p),
+// R(2p+1)); the packed window rows come from gP[i].w.
+template <int TILE, int NT, bool YT>
 __device__ __forceinline__ void stage_rowpairs(int nb, const float4* gB, const float4* gP,
                                                float4* rq) {
   constexpr int HP = TILE / 2;
@@ -122,7 +233,7 @@ __device__ __forceinline__ void stage_rowpairs(int nb, const float4* gB, const f
     float R0 = fmaf(b.z * Y0, Y0, b.w), R1 = fmaf(b.z * Y1, Y1, b.w);
     if (r0 < ly0 || r0 > ly1) R0 = -kInf;
     if (r1 < ly0 || r1 > ly1) R1 = -kInf;
-    rq[idx] = make_float4(-b.y * Y0, -b.y * Y1, R0, R1);
+    rq[idx] = YT ? make_float4(Y0, Y1, R0, R1) : make_float4(-b.y * Y0, -b.y * Y1, R0, R1);
   }
 }
 
@@ -160,17 +271,17 @@ __device__ __forceinline__ void fwd_gaussian(float2 (&acc)[NQ][3], const FwdOps<
   }
 }
 
-template <int TILE, int BY, int PF>
+template <int TILE, int BY, int PF, bool GRID>
 __global__ void __launch_bounds__(TILE * TILE / BY) k_raster_fwd(Ws w, const uint32_t* vals) {
   constexpr int NT = TILE * TILE / BY, BATCH = NT * PF, NQ = BY / 2, HP = TILE / 2;
   __shared__ __align__(16) float4 raw[2][BATCH * kRecordF4];
   __shared__ float4 gA[BATCH], gB[BATCH], gC[BATCH];
   __shared__ float4 rq[BATCH * HP];
+  __shared__ uint32_t qbuf[GRID ? GridSource<NT, PF>::QCAP : 1];
 
   const ImageDesc* D;
   int ox, oy;
   tile_origin<TILE>(w, blockIdx.x, D, ox, oy);
-  const uint2 range = w.ranges[blockIdx.x];
   const int col = threadIdx.x % TILE;
   const int row0 = (threadIdx.x / TILE) * BY;
   const int pair0 = row0 / 2;
@@ -180,13 +291,57 @@ __global__ void __launch_bounds__(TILE * TILE / BY) k_raster_fwd(Ws w, const uin
 #pragma unroll
   for (int j = 0; j < NQ; ++j) acc[j][0] = acc[j][1] = acc[j][2] = f2(0.0f, 0.0f);
 
-  const int start = (int)range.x, total = (int)range.y - start;
+  typename std::conditional<GRID, GridSource<NT, PF>, SortedSource<NT, PF>>::type src;
+  // grid mode: the tile's slice [lbase, lbase + lcount) of the pair list, where
+  // the forward leaves its Gaussian ids (ascending) for the adjoint
+  __shared__ int sl_base;
+  int lbase = 0, lcount = 0, lpos = 0;
+  bool lok = false;
+  if constexpr (GRID) {
+    grid_source_init<TILE, NT, PF>(w, D, ox, oy, qbuf, src);
+    lcount = (int)w.tcount[blockIdx.x];
+    if (threadIdx.x == 0) {
+      const unsigned long long b = atomicAdd(&w.hdr->list_cursor, (unsigned long long)lcount);
+      const bool fits = b + (unsigned long long)lcount <= (unsigned long long)w.capacity;
+      sl_base = fits ? (int)b : -1;
+      w.ranges[blockIdx.x] = fits ? make_uint2((uint32_t)b, (uint32_t)(b + lcount)) : make_uint2(0u, 0u);
+      if (!fits && lcount > 0) atomicOr(&w.hdr->status, kStCapacity);
+    }
+    __syncthreads();
+    lbase = sl_base;
+    lok = lbase >= 0;
+  } else {
+    const uint2 range = w.ranges[blockIdx.x];
+    src.vals = vals;
+    src.pos = (int)range.x;
+    src.end = (int)range.y;
+  }
+  // grid mode: append a batch of ids to the tile's slice of the list
+  auto keep = [&](const uint32_t (&ids)[PF], int n) {
+    if constexpr (GRID) {
+      if (lpos + n > lcount) {   // the footprint count and the tile test disagree
+        if (threadIdx.x == 0) atomicOr(&w.hdr->status, kStInternal);
+        lok = false;
+      }
+      if (lok) {
+#pragma unroll
+        for (int j = 0; j < PF; ++j) {
+          const int i = j * NT + threadIdx.x;
+          if (i < n) w.vals[0][lbase + lpos + i] = ids[j];
+        }
+      }
+      lpos += n;
+    }
+  };
+  // batches of the tile's `total` Gaussians (grid mode: the footprint count)
+  int total;
+  if constexpr (GRID) total = lcount; else total = src.end - src.pos;
   const int nbat = (total + BATCH - 1) / BATCH;
   uint32_t gid[PF];
   if (nbat > 0) {
-    load_ids<NT, PF>(vals, start, min(BATCH, total), gid);
+    keep(gid, src.next(gid));                              // batch 0
     issue_records<NT, PF>(w, gid, min(BATCH, total), raw[0]);
-    if (nbat > 1) load_ids<NT, PF>(vals, start + BATCH, min(BATCH, total - BATCH), gid);
+    if (nbat > 1) keep(gid, src.next(gid));                // batch 1
   }
   for (int b = 0; b < nbat; ++b) {
     const int nb = min(BATCH, total - b * BATCH);
@@ -194,12 +349,11 @@ __global__ void __launch_bounds__(TILE * TILE / BY) k_raster_fwd(Ws w, const uin
     __syncthreads();
     stage_records<TILE, NT, false>(raw[b & 1], nb, ox, oy, gA, gB, gC, nullptr);
     __syncthreads();
-    stage_rowpairs<TILE, NT>(nb, gB, gC, rq);
+    stage_rowpairs<TILE, NT, false>(nb, gB, gC, rq);
     __syncthreads();
     if (b + 1 < nbat) {
       issue_records<NT, PF>(w, gid, min(BATCH, total - (b + 1) * BATCH), raw[(b + 1) & 1]);
-      if (b + 2 < nbat)
-        load_ids<NT, PF>(vals, start + (b + 2) * BATCH, min(BATCH, total - (b + 2) * BATCH), gid);
+      if (b + 2 < nbat) keep(gid, src.next(gid));          // batch b + 2
     }
     // Two operand sets in registers: Gaussian i + 1's loads overlap i's math.
     FwdOps<NQ> A, B;
@@ -237,17 +391,19 @@ __global__ void __launch_bounds__(TILE * TILE / BY) k_raster_fwd(Ws w, const uin
 // accumulates, over its pixels, with Gw = (g . c) 2^e,
 //   SY = sum Gw Y, SYY = sum Gw Y^2, C_k = sum g_k 2^e,
 // and forms S0 = sum Gw = c . C, then (its X is fixed) SX = X S0, SXX = X SX,
-// SXY = X SY. Y = y - cy is rebuilt per pixel from the thread's first row.
+// SXY = X SY. Y = y - cy comes with the row terms (d = sA X - sK Y is then
+// one FFMA2 per row pair).
 // Eight values per Gaussian leave the tile (SX, SY, SXX, SXY, SYY, C_r, C_g,
 // C_b); S0 is linear in C (S0 = c . C) and is rebuilt from the summed C.
 // Reduction over each warp's 32 lanes, batched over kRB = 4 Gaussians (32
 // rows): lanes store their eight values transposed in shared memory (row
-// (g, f) holds the 32 lane values, padded to 33 floats so that no two lanes
-// read one bank), then lane j sums row j and adds the total to the Gaussian's
-// record-space accumulator: one atomic per (tile, Gaussian, value) and warp.
+// (g, f) holds the 32 lane values, padded to 36 floats so that rows start on
+// 16-byte boundaries), then lane j sums row j with eight 16-byte loads and
+// adds the total to the Gaussian's record-space accumulator: one atomic per
+// (tile, Gaussian, value) and warp.
 constexpr int kNV = 8;            // values per Gaussian leaving a tile
 constexpr int kRB = 4;            // Gaussians per reduction round (kRB * kNV = 32 rows)
-constexpr int kRedRow = 33;       // padded row of 32 lane values
+constexpr int kRedRow = 36;       // row of 32 lane values, padded to a 16-byte multiple
 
 template <int NQ>
 struct BwdOps {
@@ -263,25 +419,22 @@ struct BwdOps {
   }
 };
 
-// The nine record-space moments of one Gaussian over this thread's pixels,
+// The eight record-space moments of one Gaussian over this thread's pixels,
 // two rows at a time in packed FP32x2 arithmetic. g[j][ch] holds dL/dI of
 // channel ch at rows (2j, 2j + 1).
 template <int NQ>
 __device__ __forceinline__ void bwd_gaussian(const float2 (&g)[NQ][3], const BwdOps<NQ>& o,
-                                             float fcol, int row0, float (&v)[kNV]) {
+                                             float fcol, float (&v)[kNV]) {
   const float Xr = fcol - o.a.x;
   const float Xs = (fcol < o.a.z || fcol > o.a.w) ? kInf : o.a.y * Xr;
   const float2 X2 = f2(Xs, Xs);
-  const float Y0 = (float)row0 - o.e.z;
-  const float2 Yb = f2(Y0, Y0 + 1.0f);
+  const float2 nsK = f2(o.e.z, o.e.z);
   const float2 cr = f2(o.c.x, o.c.y), cg = f2(o.c.z, o.c.w), cb = f2(o.e.x, o.e.y);
-  // Y moments about the centre, accumulated per pixel (rebuilding them from
-  // moments in the row offset would cancel when the rows are far from cy).
   float2 SY = f2(0.f, 0.f), SYY = SY, Cr = SY, Cg = SY, Cb = SY;
 #pragma unroll
   for (int j = 0; j < NQ; ++j) {
-    const float2 Y = __fadd2_rn(Yb, f2(2.0f * j, 2.0f * j));
-    const float2 d = __fadd2_rn(X2, f2(o.q[j].x, o.q[j].y));
+    const float2 Y = f2(o.q[j].x, o.q[j].y);
+    const float2 d = __ffma2_rn(nsK, Y, X2);
     const float2 e = __ffma2_rn(f2(-d.x, -d.y), d, f2(o.q[j].z, o.q[j].w));
     const float2 wv = f2(ex2_approx(e.x), ex2_approx(e.y));
     const float2 G = __ffma2_rn(g[j][2], cb, __ffma2_rn(g[j][1], cg, __fmul2_rn(g[j][0], cr)));
@@ -311,14 +464,20 @@ __global__ void __launch_bounds__(TILE * TILE / BY) k_raster_bwd(Ws w, const uin
   __shared__ __align__(16) float4 raw[2][BATCH * kRecordF4];
   __shared__ float4 gA[BATCH], gB[BATCH], gC[BATCH], gD[BATCH];
   __shared__ float4 rq[BATCH * HP];
-  __shared__ float red[NW][kRB * kNV * kRedRow];
+  __shared__ __align__(16) float red[NW][kRB * kNV * kRedRow];
   __shared__ uint32_t gids[2][BATCH];
 
   const ImageDesc* D;
   int ox, oy;
   tile_origin<TILE>(w, blockIdx.x, D, ox, oy);
-  const uint2 range = w.ranges[blockIdx.x];
-  if (range.y <= range.x) return;
+  SortedSource<NT, PF> src;
+  {
+    const uint2 range = w.ranges[blockIdx.x];
+    if (range.y <= range.x) return;
+    src.vals = vals;
+    src.pos = (int)range.x;
+    src.end = (int)range.y;
+  }
   const int col = threadIdx.x % TILE;
   const int row0 = (threadIdx.x / TILE) * BY;
   const int pair0 = row0 / 2;
@@ -346,29 +505,28 @@ __global__ void __launch_bounds__(TILE * TILE / BY) k_raster_bwd(Ws w, const uin
     }
   }
 
-  const int start = (int)range.x, total = (int)range.y - start;
-  const int nbat = (total + BATCH - 1) / BATCH;
   uint32_t gid[PF];
-  load_ids<NT, PF>(vals, start, min(BATCH, total), gid);
+  int nb = src.next(gid);      // batch 0
+  int nb1 = 0;
+  if (nb > 0) {
 #pragma unroll
-  for (int j = 0; j < PF; ++j) gids[0][j * NT + threadIdx.x] = gid[j];
-  issue_records<NT, PF>(w, gid, min(BATCH, total), raw[0]);
-  if (nbat > 1) load_ids<NT, PF>(vals, start + BATCH, min(BATCH, total - BATCH), gid);
-
-  for (int b = 0; b < nbat; ++b) {
-    const int nb = min(BATCH, total - b * BATCH);
+    for (int j = 0; j < PF; ++j) gids[0][j * NT + threadIdx.x] = gid[j];
+    issue_records<NT, PF>(w, gid, nb, raw[0]);
+    nb1 = src.next(gid);        // batch 1
+  }
+  for (int b = 0; nb > 0; ++b) {
     cp_async_wait_all();
     __syncthreads();
     stage_records<TILE, NT, true>(raw[b & 1], nb, ox, oy, gA, gB, gC, gD);
     __syncthreads();
-    stage_rowpairs<TILE, NT>(nb, gB, gD, rq);
+    stage_rowpairs<TILE, NT, true>(nb, gB, gD, rq);
     __syncthreads();
-    if (b + 1 < nbat) {
+    int nb2 = 0;
+    if (nb1 > 0) {
 #pragma unroll
       for (int j = 0; j < PF; ++j) gids[(b + 1) & 1][j * NT + threadIdx.x] = gid[j];
-      issue_records<NT, PF>(w, gid, min(BATCH, total - (b + 1) * BATCH), raw[(b + 1) & 1]);
-      if (b + 2 < nbat)
-        load_ids<NT, PF>(vals, start + (b + 2) * BATCH, min(BATCH, total - (b + 2) * BATCH), gid);
+      issue_records<NT, PF>(w, gid, nb1, raw[(b + 1) & 1]);
+      nb2 = src.next(gid);      // batch b + 2
     }
     const uint32_t* bgid = gids[b & 1];
     // One Gaussian: its moments, staged for the warp reduction; every kRB
@@ -377,21 +535,22 @@ __global__ void __launch_bounds__(TILE * TILE / BY) k_raster_bwd(Ws w, const uin
       float v[kNV] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       const int pk = __float_as_int(o.e.w);
       if (NW == 1 || ((pk >> 16) >= wrow0 && (pk & 0xffff) <= wrow1))   // warp-uniform
-        bwd_gaussian<NQ>(g, o, fcol, row0, v);
+        bwd_gaussian<NQ>(g, o, fcol, v);
       const int slot = i % kRB;
 #pragma unroll
       for (int f = 0; f < kNV; ++f) wred[(slot * kNV + f) * kRedRow + lane] = v[f];
       if (slot == kRB - 1 || i == nb - 1) {   // block-uniform
         __syncwarp();
         if (lane < (slot + 1) * kNV) {
-          const float* src = wred + lane * kRedRow;
+          const float4* src = reinterpret_cast<const float4*>(wred + lane * kRedRow);
           float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
 #pragma unroll
-          for (int l = 0; l < 32; l += 4) {
-            s0 += src[l];
-            s1 += src[l + 1];
-            s2 += src[l + 2];
-            s3 += src[l + 3];
+          for (int l = 0; l < 8; ++l) {
+            const float4 t = src[l];
+            s0 += t.x;
+            s1 += t.y;
+            s2 += t.z;
+            s3 += t.w;
           }
           const float s = (s0 + s1) + (s2 + s3);
           const int gi = i - slot + lane / kNV;
@@ -411,6 +570,8 @@ __global__ void __launch_bounds__(TILE * TILE / BY) k_raster_bwd(Ws w, const uin
       process(B, i + 1);
     }
     __syncthreads();
+    nb = nb1;
+    nb1 = nb2;
   }
 }
 
@@ -422,7 +583,8 @@ cudaError_t run(const Ws& w, const uint32_t* vals, bool bwd, cudaStream_t s) {
     k_raster_bwd<TILE, BY, PF><<<w.tiles, NT, 0, s>>>(w, vals);
   } else {
     LaunchScope ls(kKRasterFwd, s);
-    k_raster_fwd<TILE, BY, PF><<<w.tiles, NT, 0, s>>>(w, vals);
+    if (w.grid) k_raster_fwd<TILE, BY, PF, true><<<w.tiles, NT, 0, s>>>(w, vals);
+    else k_raster_fwd<TILE, BY, PF, false><<<w.tiles, NT, 0, s>>>(w, vals);
   }
   return cudaGetLastError();
 }

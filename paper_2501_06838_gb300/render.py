@@ -75,7 +75,7 @@ def _struct_v(v, tile: int = 0, batch: int = 0, adjoint: int = 0) -> _abi.GsView
     return _abi.GsView(int(v.lr_h), int(v.lr_w), int(v.out_h), int(v.out_w), float(v.scale),
                        float(getattr(v, "trunc_k", 3.0)), int(getattr(v, "norm", 0)),
                        int(tile), int(batch), int(getattr(v, "window", 0)),
-                       int(getattr(v, "align", 0)), int(adjoint))
+                       int(getattr(v, "align", 0)), int(adjoint), int(getattr(v, "binning", 0)), 0)
 
 
 def _arrays(gs: Sequence[Gaussians], views, tile=0, batch=0):

@@ -38,12 +38,18 @@ def test_host_only_entry_points(lib):
     assert lib.gs_version().startswith(b"gs ")
     assert lib.gs_kernel_name(9) == b"raster_fwd"
     G = (_abi.GsGaussians * 1)(_abi.GsGaussians(1, 1, 1, 1, 1, 2304, 0, 1))
-    V = (_abi.GsView * 1)(_abi.GsView(48, 48, 192, 192, 4.0, 3.0, 0, 16, 64, 0, 0, 0))
+    V = (_abi.GsView * 1)(_abi.GsView(48, 48, 192, 192, 4.0, 3.0, 0, 16, 64, 0, 0, 0,
+                                      _abi.GS_BINNING_SORT, 0))
     a = lib.gs_workspace_size(1, G, V, 0)
     b = lib.gs_workspace_size(1, G, V, 100000)
     assert 0 < a < b
     # 4 u32 arrays per pair plus the radix histograms
     assert b - a >= 16 * 100000
+    # grid binning keeps one pair array (the per-tile lists) and no sort buffers
+    V[0].binning = _abi.GS_BINNING_GRID
+    ga, gb = lib.gs_workspace_size(1, G, V, 0), lib.gs_workspace_size(1, G, V, 100000)
+    assert 4 * 100000 <= gb - ga < b - a
+    V[0].binning = _abi.GS_BINNING_SORT
     # invalid requests return 0 with a message
     V[0].tile = 12
     assert lib.gs_workspace_size(1, G, V, 0) == 0

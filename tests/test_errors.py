@@ -75,6 +75,7 @@ def test_capacity_overflow_flagged():
     import torch
     import paper_2501_06838_gb300 as gs
     g, v = S.config1()[0][0], S.config1()[1][0]
+    v.binning = 1   # the sorted pair list: its capacity is what can overflow
     dg = device_gaussians(g)
     need = gs.count_pairs([dg], [v])
     ws = gs.Workspace(gs.workspace_bytes([dg], [v], need // 2))
@@ -86,6 +87,18 @@ def test_capacity_overflow_flagged():
     ws_ok = gs.Workspace(gs.workspace_bytes([dg], [v], need))
     out2, _ = gs.render(dg, v, ws=ws_ok, check=True)
     assert out2.abs().max() > 0
+    # grid binning: the forward needs no pair list and still renders in full;
+    # the per-tile lists it leaves for the adjoint do not fit, which is flagged
+    v.binning = 2
+    ws_grid = gs.Workspace(gs.workspace_bytes([dg], [v], need // 2))
+    out3, _ = gs.render(dg, v, ws=ws_grid)
+    with pytest.raises(gs.GsError) as ei:
+        gs.sync_status(ws_grid)
+    assert ei.value.status == 2
+    assert torch.equal(out3, out2)
+    ws_grid_ok = gs.Workspace(gs.workspace_bytes([dg], [v], need))
+    out4, _ = gs.render(dg, v, ws=ws_grid_ok, check=True)
+    assert torch.equal(out4, out2)
 
 
 @pytest.mark.gpu
