@@ -77,8 +77,23 @@ def storage_array(x64: np.ndarray, dtype: str) -> np.ndarray:
 
 
 @dataclasses.dataclass
+class Head:
+    """The Gaussian primary head's activations (Sec. 3.2), fused into the
+    renderer: sigma = sigma_lo + sigma_span * sigmoid(raw), rho = rho_scale *
+    tanh(raw), c = sigmoid(raw), alpha = sigmoid(raw), o = offset_scale * raw
+    (or offset_scale * tanh(raw) with offset_tanh). The paper's own head is
+    sigma_lo = 0, sigma_span = 1, rho_scale = 1, offset_scale = 1, no tanh."""
+    sigma_lo: float = 0.0
+    sigma_span: float = 1.0
+    rho_scale: float = 1.0
+    offset_scale: float = 1.0
+    offset_tanh: int = 0
+
+
+@dataclasses.dataclass
 class GaussianSet:
-    """Physical (post-activation) Gaussian parameters of one image.
+    """Gaussian parameters of one image: physical (post-activation) values, or
+    raw head outputs when `head` is set.
 
     Arrays hold the STORED values widened exactly to float64: what the renderer
     reads. `originals` keeps the float32 originals when `dtype` is reduced.
@@ -95,6 +110,7 @@ class GaussianSet:
     ref_grid_m: int = 1
     dtype: str = "f32"
     originals: "GaussianSet | None" = None
+    head: "Head | None" = None
 
     @property
     def n(self) -> int:
@@ -112,7 +128,7 @@ class GaussianSet:
         vals = [storage_round(a, dtype) for a in base.fields()]
         return GaussianSet(*vals, lr_h=base.lr_h, lr_w=base.lr_w,
                            ref_grid_m=base.ref_grid_m, dtype=dtype,
-                           originals=None if dtype == "f32" else base)
+                           originals=None if dtype == "f32" else base, head=base.head)
 
     def subset(self, idx) -> "GaussianSet":
         idx = np.asarray(idx)
@@ -159,6 +175,21 @@ def draw_gaussians(seed: int, lr_h: int, lr_w: int, m: int = 1,
     alpha = u[:, 8].copy()
     f32 = GaussianSet(*(storage_round(a, "f32") for a in (offset, sigma, rho, rgb, alpha)),
                       lr_h=lr_h, lr_w=lr_w, ref_grid_m=m, dtype="f32")
+    return f32 if dtype == "f32" else f32.with_dtype(dtype)
+
+
+def draw_raw_head(seed: int, lr_h: int, lr_w: int, m: int = 1, head: Head | None = None,
+                  dtype: str = "f32", spread: float = 1.5) -> GaussianSet:
+    """Raw head outputs ~ N(0, spread^2) per value (offsets ~ N(0, (0.25/sqrt m)^2)),
+    for the fused-head render: the set's `head` maps them to physical values."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = m * lr_h * lr_w
+    z = rng.standard_normal((n, 9))
+    offset = z[:, 0:2] * (0.25 / math.sqrt(m))
+    sigma, rho = z[:, 2:4] * spread, z[:, 4] * spread
+    rgb, alpha = z[:, 5:8] * spread, z[:, 8] * spread
+    f32 = GaussianSet(*(storage_round(a, "f32") for a in (offset, sigma, rho, rgb, alpha)),
+                      lr_h=lr_h, lr_w=lr_w, ref_grid_m=m, dtype="f32", head=head or Head())
     return f32 if dtype == "f32" else f32.with_dtype(dtype)
 
 

@@ -32,6 +32,16 @@
 // sub-grid of each LR pixel (Sec. 3.2, Gaussian Embedding). With m = 0 the
 // offset array holds mu itself.
 //
+// Fused Gaussian head (Sec. 3.2, Gaussian Primary Head), optional: the five
+// arrays then hold raw head outputs, mapped to the physical parameters by
+//   sigma = lo + span * sigmoid(raw), rho = rho_scale * tanh(raw),
+//   c = sigmoid(raw), alpha = sigmoid(raw),
+//   o = offset_scale * raw  (or offset_scale * tanh(raw)),
+// in FP64 for the density and its derivatives. The window, an integer
+// decision, takes sigma and o from one fixed sequence of float32 operations
+// (exp by Cody-Waite reduction and a Taylor polynomial, see exp_f32), which
+// the GPU follows operation for operation.
+//
 // Adjoint: hand-derived derivatives of the loss L = sum g * I with the windows
 // R_i held fixed (the derivative of a moving window edge is not part of it).
 // A templated complex-step path differentiates the same forward independently.
@@ -45,6 +55,7 @@
 #include <complex>
 #include <cstdint>
 #include <cstring>
+#include <memory>
 #include <thread>
 #include <vector>
 
@@ -61,6 +72,54 @@ struct OView {
 };
 
 struct Rect { int32_t x0, x1, y0, y1; };  // inclusive; empty when x0 > x1
+
+struct OHead {
+  float sigma_lo, sigma_span, rho_scale, offset_scale;
+  int32_t offset_tanh;   // 0: o = offset_scale * raw, 1: o = offset_scale * tanh(raw)
+  int32_t pad[3];
+};
+
+// e^x in float32 by Cody-Waite range reduction (x = n ln2 + r, ln2 split into
+// a 9-bit head and a tail so that n * head is exact) and the degree-7 Taylor
+// polynomial of e^r on |r| <= ln2 / 2, each operation one float32 rounding
+// (the build disables contraction). Relative error a few ulp.
+float exp_f32(float x) {
+  const float kL2E = 1.44269502162933349609375f;
+  const float kLn2Hi = 0.693359375f;
+  const float kLn2Lo = -2.12194441701285541057586669921875e-4f;
+  if (x < -87.0f) x = -87.0f;
+  if (x > 88.0f) x = 88.0f;
+  volatile float t = x * kL2E;
+  const float n = std::rint((float)t);
+  volatile float a = n * kLn2Hi;
+  volatile float b = n * kLn2Lo;
+  volatile float r0 = x - a;
+  volatile float r = r0 - b;
+  const float c[8] = {1.0f, 1.0f, 0.5f, 0.16666667163372039794921875f, 4.1666667908430099487304688e-2f,
+                      8.3333337679505348205566406e-3f, 1.3888889225199818611145020e-3f,
+                      1.9841270113829523324966431e-4f};
+  volatile float p = c[7];
+  for (int k = 6; k >= 0; --k) {
+    volatile float pr = p * (float)r;
+    p = pr + c[k];
+  }
+  return std::ldexp((float)p, (int)n);
+}
+
+float sigmoid_f32(float x) {
+  volatile float e = exp_f32(-x);
+  volatile float d = 1.0f + e;
+  return 1.0f / (float)d;
+}
+
+float tanh_f32(float x) {
+  const float ax = std::fabs(x);
+  volatile float e = exp_f32(-2.0f * ax);
+  volatile float num = 1.0f - e;
+  volatile float den = 1.0f + e;
+  const float t = (float)num / (float)den;
+  return x < 0.0f ? -t : t;
+}
 
 int isqrt_exact(int m) {
   for (int r = 1; r * r <= m; ++r) if (r * r == m) return r;
@@ -126,10 +185,67 @@ void rect_axis_f32(float c, float sigma, float s, float k, int window, int lr_ex
 struct Params {
   const double *off, *sig, *rho, *rgb, *alpha;
   int64_t n;
+  const double *woff = nullptr, *wsig = nullptr;   // window-defining o, sigma (default: off, sig)
+  double woff_at(int64_t k) const { return woff ? woff[k] : off[k]; }
+  double wsig_at(int64_t k) const { return wsig ? wsig[k] : sig[k]; }
 };
 
+double sigmoid64(double x) { return 1.0 / (1.0 + std::exp(-x)); }
+
+// The physical parameters (FP64) and the window-defining float32 ones of a set
+// whose arrays hold raw head outputs.
+struct HeadMapped {
+  std::vector<double> off, sig, rho, rgb, alpha, woff, wsig;
+  HeadMapped(const double* o, const double* sg, const double* rh, const double* c, const double* a,
+             int64_t n, const OHead& H)
+      : off(2 * n), sig(2 * n), rho(n), rgb(3 * n), alpha(n), woff(2 * n), wsig(2 * n) {
+    for (int64_t i = 0; i < n; ++i) {
+      for (int k = 0; k < 2; ++k) {
+        const double ro = o[2 * i + k], rs = sg[2 * i + k];
+        off[2 * i + k] = H.offset_tanh ? (double)H.offset_scale * std::tanh(ro) : (double)H.offset_scale * ro;
+        const float o32 = (float)ro;
+        volatile float wo = H.offset_tanh ? H.offset_scale * tanh_f32(o32) : H.offset_scale * o32;
+        woff[2 * i + k] = (double)(float)wo;
+        sig[2 * i + k] = (double)H.sigma_lo + (double)H.sigma_span * sigmoid64(rs);
+        volatile float sp = H.sigma_span * sigmoid_f32((float)rs);
+        volatile float ws = H.sigma_lo + (float)sp;
+        wsig[2 * i + k] = (double)(float)ws;
+      }
+      rho[i] = (double)H.rho_scale * std::tanh(rh[i]);
+      for (int k = 0; k < 3; ++k) rgb[3 * i + k] = sigmoid64(c[3 * i + k]);
+      alpha[i] = sigmoid64(a[i]);
+    }
+  }
+  Params params(int64_t n) const {
+    Params P{off.data(), sig.data(), rho.data(), rgb.data(), alpha.data(), n};
+    P.woff = woff.data();
+    P.wsig = wsig.data();
+    return P;
+  }
+};
+
+// d(physical)/d(raw) of the head, per Gaussian and parameter in the gradient
+// order (o_x, o_y, sigma_x, sigma_y, rho, r, g, b, alpha).
+void head_jacobian(const double* o, const double* sg, const double* rh, const double* c,
+                   const double* a, int64_t i, const OHead& H, double* J) {
+  for (int k = 0; k < 2; ++k) {
+    const double t = std::tanh(o[2 * i + k]);
+    J[k] = H.offset_tanh ? (double)H.offset_scale * (1.0 - t * t) : (double)H.offset_scale;
+    const double sv = sigmoid64(sg[2 * i + k]);
+    J[2 + k] = (double)H.sigma_span * sv * (1.0 - sv);
+  }
+  const double tr = std::tanh(rh[i]);
+  J[4] = (double)H.rho_scale * (1.0 - tr * tr);
+  for (int k = 0; k < 3; ++k) {
+    const double sc = sigmoid64(c[3 * i + k]);
+    J[5 + k] = sc * (1.0 - sc);
+  }
+  const double sa = sigmoid64(a[i]);
+  J[8] = sa * (1.0 - sa);
+}
+
 void centre_f32(const Params& P, const OView& V, int64_t i, float* mx, float* my) {
-  float ox = (float)P.off[2 * i], oy = (float)P.off[2 * i + 1];
+  float ox = (float)P.woff_at(2 * i), oy = (float)P.woff_at(2 * i + 1);
   if (V.ref_grid_m > 0) {
     float px, py;
     ref_pos(i, V.ref_grid_m, V.lr_w, &px, &py);
@@ -157,8 +273,9 @@ Rect rect_of(const Params& P, const OView& V, int64_t i) {
   float mx, my;
   centre_f32(P, V, i, &mx, &my);
   const float cx = hr_centre_f32(mx, V.scale, V.align), cy = hr_centre_f32(my, V.scale, V.align);
-  rect_axis_f32(cx, (float)P.sig[2 * i], V.scale, V.trunc_k, V.window, V.lr_w, V.out_w, &R.x0, &R.x1);
-  rect_axis_f32(cy, (float)P.sig[2 * i + 1], V.scale, V.trunc_k, V.window, V.lr_h, V.out_h, &R.y0,
+  rect_axis_f32(cx, (float)P.wsig_at(2 * i), V.scale, V.trunc_k, V.window, V.lr_w, V.out_w, &R.x0,
+                &R.x1);
+  rect_axis_f32(cy, (float)P.wsig_at(2 * i + 1), V.scale, V.trunc_k, V.window, V.lr_h, V.out_h, &R.y0,
                 &R.y1);
   return R;
 }
@@ -174,8 +291,8 @@ bool inside_f32(const Params& P, const OView& V, int64_t i, int x, int y) {
   float s = V.scale, k = V.trunc_k;
   volatile float cx = hr_centre_f32(mx, s, V.align), cy = hr_centre_f32(my, s, V.align);
   volatile float sk = s * k;
-  volatile float rx = V.window == 0 ? sk * (float)P.sig[2 * i] : sk * (float)V.lr_w;
-  volatile float ry = V.window == 0 ? sk * (float)P.sig[2 * i + 1] : sk * (float)V.lr_h;
+  volatile float rx = V.window == 0 ? sk * (float)P.wsig_at(2 * i) : sk * (float)V.lr_w;
+  volatile float ry = V.window == 0 ? sk * (float)P.wsig_at(2 * i + 1) : sk * (float)V.lr_h;
   volatile float ax = cx - rx, bx = cx + rx, ay = cy - ry, by = cy + ry;
   float fx = (float)x, fy = (float)y;
   if (V.window == 0) return fx >= ax && fx <= bx && fy >= ay && fy <= by;
@@ -245,15 +362,35 @@ bool valid_view(const OView* V) {
   return true;
 }
 
+// Params over either physical arrays or raw head outputs (then mapped).
+struct ParamSet {
+  std::unique_ptr<HeadMapped> hm;
+  Params P;
+  ParamSet(const double* off, const double* sig, const double* rho, const double* rgb,
+           const double* alpha, int64_t n, const OHead* head)
+      : P{off, sig, rho, rgb, alpha, n} {
+    if (head) {
+      hm.reset(new HeadMapped(off, sig, rho, rgb, alpha, n, *head));
+      P = hm->params(n);
+    }
+  }
+};
+
+bool valid_head(const OHead* H) {
+  return !H || (H->sigma_span > 0.0f && H->sigma_lo >= 0.0f && std::fabs(H->rho_scale) <= 1.0f &&
+                (H->offset_tanh == 0 || H->offset_tanh == 1));
+}
+
 }  // namespace
 
 extern "C" {
 
 // Integer rectangles R_i, [n][4] = (x0, x1, y0, y1), inclusive (empty: x0 > x1).
 int gso_rects(const double* off, const double* sig, const double* rho, const double* rgb,
-              const double* alpha, int64_t n, const OView* V, int32_t* rects) {
-  if (!valid_view(V)) return 1;
-  Params P{off, sig, rho, rgb, alpha, n};
+              const double* alpha, int64_t n, const OView* V, const OHead* head, int32_t* rects) {
+  if (!valid_view(V) || !valid_head(head)) return 1;
+  ParamSet PS(off, sig, rho, rgb, alpha, n, head);
+  const Params& P = PS.P;
   for (int64_t i = 0; i < n; ++i) {
     Rect R = rect_of(P, *V, i);
     rects[4 * i] = R.x0; rects[4 * i + 1] = R.x1; rects[4 * i + 2] = R.y0; rects[4 * i + 3] = R.y1;
@@ -267,10 +404,11 @@ int gso_rects(const double* off, const double* sig, const double* rho, const dou
 // mode 1: all pairs: every pixel against every Gaussian, float32 membership test.
 // rects_in (optional, [n][4]) overrides R_i (frozen windows for derivative tests).
 int gso_render(const double* off, const double* sig, const double* rho, const double* rgb,
-               const double* alpha, int64_t n, const OView* V, int mode, int threads,
-               const int32_t* rects_in, double* out) {
-  if (!valid_view(V)) return 1;
-  Params P{off, sig, rho, rgb, alpha, n};
+               const double* alpha, int64_t n, const OView* V, const OHead* head, int mode,
+               int threads, const int32_t* rects_in, double* out) {
+  if (!valid_view(V) || !valid_head(head)) return 1;
+  ParamSet PS(off, sig, rho, rgb, alpha, n, head);
+  const Params& P = PS.P;
   const OView v = *V;
   const int64_t H = v.out_h, W = v.out_w;
   std::memset(out, 0, sizeof(double) * 3 * H * W);
@@ -325,10 +463,11 @@ int gso_render(const double* off, const double* sig, const double* rho, const do
 //   density: dlogZ/dsx = -1/sx, dlogZ/dsy = -1/sy, dlogZ/drho = rho/D; peak: 0.
 //   mu = p + o, so dL/do = dL/dmu.
 int gso_adjoint(const double* off, const double* sig, const double* rho, const double* rgb,
-                const double* alpha, int64_t n, const OView* V, const double* grad_out,
-                int threads, const int32_t* rects_in, double* grads) {
-  if (!valid_view(V)) return 1;
-  Params P{off, sig, rho, rgb, alpha, n};
+                const double* alpha, int64_t n, const OView* V, const OHead* head,
+                const double* grad_out, int threads, const int32_t* rects_in, double* grads) {
+  if (!valid_view(V) || !valid_head(head)) return 1;
+  ParamSet PS(off, sig, rho, rgb, alpha, n, head);
+  const Params& P = PS.P;
   const OView v = *V;
   const int64_t H = v.out_h, W = v.out_w;
   const double s = (double)v.scale;
@@ -370,6 +509,11 @@ int gso_adjoint(const double* off, const double* sig, const double* rho, const d
             acc[8] += G * f;
           }
       }
+      if (head) {   // chain rule through the head's activations
+        double J[9];
+        head_jacobian(off, sig, rho, rgb, alpha, i, *head, J);
+        for (int k = 0; k < 9; ++k) acc[k] *= J[k];
+      }
       for (int k = 0; k < 9; ++k) grads[9 * i + k] = acc[k];
     }
   });
@@ -380,14 +524,17 @@ int gso_adjoint(const double* off, const double* sig, const double* rho, const d
 // dL/dtheta = Im(L(theta + i h)) / h, evaluated with the forward's own formula
 // (templated on std::complex<double>) and the frozen windows. grads[k][9].
 int gso_complex_step(const double* off, const double* sig, const double* rho, const double* rgb,
-                     const double* alpha, int64_t n, const OView* V, const double* grad_out,
-                     const int64_t* gids, int64_t k, double h, double* grads) {
-  if (!valid_view(V)) return 1;
-  Params P{off, sig, rho, rgb, alpha, n};
+                     const double* alpha, int64_t n, const OView* V, const OHead* head,
+                     const double* grad_out, const int64_t* gids, int64_t k, double h,
+                     double* grads) {
+  if (!valid_view(V) || !valid_head(head)) return 1;
+  ParamSet PS(off, sig, rho, rgb, alpha, n, head);
+  const Params& P = PS.P;
   const OView v = *V;
   const int64_t H = v.out_h, W = v.out_w;
   const double s = (double)v.scale;
   typedef std::complex<double> C;
+  auto csig = [](C z) { return 1.0 / (1.0 + std::exp(-z)); };
   for (int64_t t = 0; t < k; ++t) {
     const int64_t i = gids[t];
     if (i < 0 || i >= n) return 2;
@@ -399,7 +546,26 @@ int gso_complex_step(const double* off, const double* sig, const double* rho, co
       for (int c = 0; c < 3; ++c) g.c[c] = g0.c[c];
       g.alpha = g0.alpha;
       const C ih(0.0, h);
-      switch (p) {
+      if (head) {   // perturb the raw head output and map it through the activations
+        const OHead& Hd = *head;
+        double px = 0.0, py = 0.0;
+        if (v.ref_grid_m > 0) {
+          float fx, fy;
+          ref_pos(i, v.ref_grid_m, v.lr_w, &fx, &fy);
+          px = fx; py = fy;
+        }
+        auto offm = [&](C z) { return Hd.offset_tanh ? (double)Hd.offset_scale * std::tanh(z)
+                                                     : (double)Hd.offset_scale * z; };
+        switch (p) {
+          case 0: g.mx = px + offm(C(off[2 * i], 0.0) + ih); break;
+          case 1: g.my = py + offm(C(off[2 * i + 1], 0.0) + ih); break;
+          case 2: g.sx = (double)Hd.sigma_lo + (double)Hd.sigma_span * csig(C(sig[2 * i], 0.0) + ih); break;
+          case 3: g.sy = (double)Hd.sigma_lo + (double)Hd.sigma_span * csig(C(sig[2 * i + 1], 0.0) + ih); break;
+          case 4: g.rho = (double)Hd.rho_scale * std::tanh(C(rho[i], 0.0) + ih); break;
+          case 5: case 6: case 7: g.c[p - 5] = csig(C(rgb[3 * i + p - 5], 0.0) + ih); break;
+          default: g.alpha = csig(C(alpha[i], 0.0) + ih); break;
+        }
+      } else switch (p) {
         case 0: g.mx += ih; break;
         case 1: g.my += ih; break;
         case 2: g.sx += ih; break;
@@ -426,19 +592,41 @@ int gso_complex_step(const double* off, const double* sig, const double* rho, co
 // One Gaussian's share of the loss, L_i = sum_{(x,y) in R_i} g(x,y) . G_i(x/s, y/s),
 // with its 9 parameters replaced by theta = (mu_x, mu_y, sigma_x, sigma_y, rho,
 // r, g, b, alpha) and R_i computed from the UNPERTURBED inputs (frozen window).
+// With a head, theta holds the raw head outputs (o_x, o_y, then the raw values
+// of sigma_x, sigma_y, rho, r, g, b, alpha), mapped through the activations.
 // Central differences of this function check the adjoint.
 double gso_gaussian_loss(const double* off, const double* sig, const double* rho, const double* rgb,
-                         const double* alpha, int64_t n, const OView* V, const double* grad_out,
-                         int64_t gid, const double* theta) {
-  if (!valid_view(V) || gid < 0 || gid >= n) return NAN;
-  Params P{off, sig, rho, rgb, alpha, n};
+                         const double* alpha, int64_t n, const OView* V, const OHead* head,
+                         const double* grad_out, int64_t gid, const double* theta) {
+  if (!valid_view(V) || !valid_head(head) || gid < 0 || gid >= n) return NAN;
+  ParamSet PS(off, sig, rho, rgb, alpha, n, head);
+  const Params& P = PS.P;
   const OView v = *V;
   const int64_t H = v.out_h, W = v.out_w;
   Rect r = rect_of(P, v, gid);
   GaussT<double> g;
-  g.mx = theta[0]; g.my = theta[1]; g.sx = theta[2]; g.sy = theta[3]; g.rho = theta[4];
-  for (int c = 0; c < 3; ++c) g.c[c] = theta[5 + c];
-  g.alpha = theta[8];
+  if (head) {
+    const OHead& Hd = *head;
+    double px = 0.0, py = 0.0;
+    if (v.ref_grid_m > 0) {
+      float fx, fy;
+      ref_pos(gid, v.ref_grid_m, v.lr_w, &fx, &fy);
+      px = fx; py = fy;
+    }
+    auto offm = [&](double z) { return Hd.offset_tanh ? (double)Hd.offset_scale * std::tanh(z)
+                                                      : (double)Hd.offset_scale * z; };
+    g.mx = px + offm(theta[0]);
+    g.my = py + offm(theta[1]);
+    g.sx = (double)Hd.sigma_lo + (double)Hd.sigma_span * sigmoid64(theta[2]);
+    g.sy = (double)Hd.sigma_lo + (double)Hd.sigma_span * sigmoid64(theta[3]);
+    g.rho = (double)Hd.rho_scale * std::tanh(theta[4]);
+    for (int c = 0; c < 3; ++c) g.c[c] = sigmoid64(theta[5 + c]);
+    g.alpha = sigmoid64(theta[8]);
+  } else {
+    g.mx = theta[0]; g.my = theta[1]; g.sx = theta[2]; g.sy = theta[3]; g.rho = theta[4];
+    for (int c = 0; c < 3; ++c) g.c[c] = theta[5 + c];
+    g.alpha = theta[8];
+  }
   double L = 0.0;
   if (r.x0 <= r.x1 && r.y0 <= r.y1)
     for (int64_t y = r.y0; y <= r.y1; ++y)
@@ -449,11 +637,31 @@ double gso_gaussian_loss(const double* off, const double* sig, const double* rho
   return L;
 }
 
-// The FP64 centre mu = p + o of Gaussian gid (p from the reference grid).
-int gso_centre(const double* off, int64_t n, const OView* V, int64_t gid, double* mu) {
-  if (!valid_view(V) || gid < 0 || gid >= n) return 1;
-  Params P{off, nullptr, nullptr, nullptr, nullptr, n};
-  centre_f64(P, *V, gid, &mu[0], &mu[1]);
+// The FP64 centre mu = p + o of Gaussian gid (p from the reference grid; with a
+// head, o from the raw offset).
+int gso_centre(const double* off, int64_t n, const OView* V, const OHead* head, int64_t gid,
+               double* mu) {
+  if (!valid_view(V) || !valid_head(head) || gid < 0 || gid >= n) return 1;
+  double o[2] = {off[2 * gid], off[2 * gid + 1]};
+  if (head)
+    for (int k = 0; k < 2; ++k)
+      o[k] = head->offset_tanh ? (double)head->offset_scale * std::tanh(o[k]) : (double)head->offset_scale * o[k];
+  double px = 0.0, py = 0.0;
+  if (V->ref_grid_m > 0) {
+    float fx, fy;
+    ref_pos(gid, V->ref_grid_m, V->lr_w, &fx, &fy);
+    px = fx; py = fy;
+  }
+  mu[0] = px + o[0];
+  mu[1] = py + o[1];
+  return 0;
+}
+
+// The window-defining float32 head activations of raw values x[n] (test hook
+// for the fixed float32 sequence): kind 0 sigmoid_f32, 1 tanh_f32, 2 exp_f32.
+int gso_head_f32(const float* x, int64_t n, int kind, float* y) {
+  for (int64_t i = 0; i < n; ++i)
+    y[i] = kind == 0 ? sigmoid_f32(x[i]) : kind == 1 ? tanh_f32(x[i]) : exp_f32(x[i]);
   return 0;
 }
 

@@ -481,3 +481,67 @@ def test_adjoint_vs_complex_step_flags(window, k, align):
     adj = oracle.adjoint(g, v, go)[ids]
     cs = oracle.complex_step(g, v, go, ids)
     np.testing.assert_allclose(adj, cs, rtol=1e-10, atol=1e-12 * np.abs(cs).max())
+
+
+# --------------------------------------------------------------------------
+# Fused Gaussian head (Sec. 3.2, Gaussian Primary Head): sigmoid for sigma, c,
+# alpha; tanh for rho; the offset as predicted (mu = p + o).
+# --------------------------------------------------------------------------
+HEAD = S.Head(sigma_lo=0.2, sigma_span=2.8, rho_scale=0.9, offset_scale=1.0, offset_tanh=0)
+
+
+def test_head_float32_sequences_accuracy():
+    """The window's float32 exp / sigmoid / tanh against numpy's float64 ones."""
+    x = np.linspace(-20, 20, 40001, dtype=np.float32)
+    e = oracle.head_f32(x, "exp").astype(np.float64)
+    ref = np.exp(x.astype(np.float64))
+    assert np.max(np.abs(e - ref) / ref) < 4 * 2.0 ** -23
+    s = oracle.head_f32(x, "sigmoid").astype(np.float64)
+    assert np.max(np.abs(s - 1 / (1 + np.exp(-x.astype(np.float64))))) < 3e-7
+    t = oracle.head_f32(x, "tanh").astype(np.float64)
+    assert np.max(np.abs(t - np.tanh(x.astype(np.float64)))) < 3e-7
+    assert np.all(np.diff(s) >= 0) and np.all(np.diff(t) >= 0)   # monotone
+
+
+@pytest.mark.parametrize("head", [HEAD, S.Head(),
+                                  S.Head(0.1, 1.5, 0.95, 0.5, offset_tanh=1)])
+def test_head_render_equals_physical_render(head):
+    """Untruncated (no window decision): the raw render equals the render of the
+    physical parameters computed with numpy's own activations."""
+    g = S.draw_raw_head(12, 10, 12, 1, head)
+    sig = lambda z: 1.0 / (1.0 + np.exp(-z))
+    f = lambda a: float(np.float32(a))   # the head's constants are float32 in the ABI
+    o = f(head.offset_scale) * (np.tanh(g.offset) if head.offset_tanh else g.offset)
+    phys = S.GaussianSet(o, f(head.sigma_lo) + f(head.sigma_span) * sig(g.sigma),
+                         f(head.rho_scale) * np.tanh(g.rho), sig(g.rgb), sig(g.alpha),
+                         g.lr_h, g.lr_w, 1)
+    v = S.View(10, 12, 27, 33, 2.75, trunc_k=0.0)
+    np.testing.assert_allclose(oracle.render(g, v), oracle.render(phys, v), rtol=1e-12, atol=1e-15)
+
+
+def test_head_windows_follow_float32_sequence():
+    """Truncated: the head's windows are those of sigma and o taken from the
+    float32 sequences (and the render matches the physical render on them)."""
+    head = S.Head(0.2, 2.8, 0.9, 1.0, offset_tanh=1)
+    g = S.draw_raw_head(13, 10, 12, 4, head)
+    s32 = np.float32(head.sigma_lo) + np.float32(head.sigma_span) * oracle.head_f32(g.sigma, "sigmoid").reshape(g.sigma.shape)
+    o32 = np.float32(head.offset_scale) * oracle.head_f32(g.offset, "tanh").reshape(g.offset.shape)
+    win = S.GaussianSet(o32.astype(np.float64), s32.astype(np.float32).astype(np.float64),
+                        np.zeros(g.n), np.ones((g.n, 3)), np.ones(g.n), g.lr_h, g.lr_w, 4)
+    v = S.View(10, 12, 30, 36, 3.0)
+    assert np.array_equal(oracle.rects(g, v), oracle.rects(win, v))
+
+
+@pytest.mark.parametrize("head", [HEAD, S.Head(0.1, 1.5, 0.95, 0.5, offset_tanh=1)])
+def test_head_adjoint_vs_complex_step_and_fd(head):
+    """Gradients with respect to the raw head outputs: hand chain rule against
+    complex-step and central differences through the activations."""
+    g = S.draw_raw_head(14, 14, 16, 1, head)
+    v = S.View(14, 16, S.out_size(14, 2.7), S.out_size(16, 2.7), 2.7)
+    go = S.grad_out(3, v.out_h, v.out_w)
+    ids = S.sample_indices(4, g.n, 25)
+    adj = oracle.adjoint(g, v, go)[ids]
+    cs = oracle.complex_step(g, v, go, ids)
+    np.testing.assert_allclose(adj, cs, rtol=1e-10, atol=1e-12 * np.abs(cs).max())
+    fd = oracle.central_difference(g, v, go, ids[:8], h=1e-5)
+    np.testing.assert_allclose(adj[:8], fd, rtol=1e-6, atol=1e-7 * np.abs(fd).max())
