@@ -119,8 +119,28 @@ typedef enum { GS_ADJOINT_AUTO = 0, GS_ADJOINT_TILE = 1, GS_ADJOINT_GAUSSIAN = 2
  * the forward is bitwise the same. */
 typedef enum { GS_BINNING_AUTO = 0, GS_BINNING_SORT = 1, GS_BINNING_GRID = 2 } gs_binning;
 
-/* Physical (post-activation) parameters of n Gaussians, structure of arrays,
- * contiguous, all of element type `dtype`. Device pointers, caller-owned. */
+/* The Gaussian primary head's activations (Sec. 3.2, "Gaussian Primary Head"),
+ * fused into the render: with a head the five arrays of gs_gaussians hold raw
+ * head outputs, mapped per Gaussian to the physical parameters
+ *   sigma = sigma_lo + sigma_span * sigmoid(raw)   (sigma_lo >= 0, sigma_span > 0)
+ *   rho   = rho_scale * tanh(raw)                  (|rho_scale| <= 1)
+ *   c     = sigmoid(raw),  alpha = sigmoid(raw)
+ *   o     = offset_scale * raw, or offset_scale * tanh(raw) with offset_tanh = 1
+ * (the paper's head: 0, 1, 1, 1, 0). The adjoint then returns dL/d(raw). The
+ * window uses sigma and o from a fixed float32 sequence (e^x by Cody-Waite
+ * reduction, ln 2 = 0.693359375 - 2.12194442e-4, and the degree-7 Taylor
+ * polynomial in Horner form; sigmoid = 1 / (1 + e^-x); tanh = (1 - e^-2|x|) /
+ * (1 + e^-2|x|) with the sign of x; every operation rounded to nearest, none
+ * fused), so that its integer edges can be reproduced exactly. */
+typedef struct gs_head {
+  float sigma_lo, sigma_span, rho_scale, offset_scale;
+  int32_t offset_tanh;   /* 0 or 1 */
+  int32_t reserved[3];   /* must be 0 */
+} gs_head;
+
+/* Parameters of n Gaussians, structure of arrays, contiguous, all of element
+ * type `dtype`: physical (post-activation) values, or raw head outputs when
+ * `head` is set. Device pointers, caller-owned. */
 typedef struct gs_gaussians {
   const void* offset; /* [n][2] o (ref_grid_m > 0) or absolute mu (ref_grid_m == 0), LR px */
   const void* sigma;  /* [n][2] (sigma_x, sigma_y) > 0, LR px */
@@ -130,6 +150,7 @@ typedef struct gs_gaussians {
   int64_t n;          /* number of Gaussians; must equal m * lr_h * lr_w when ref_grid_m > 0 */
   int32_t dtype;      /* gs_dtype of all five arrays */
   int32_t ref_grid_m; /* 0, 1, 4, 9 or 16 */
+  const gs_head* head; /* host pointer, read during the call; NULL: physical parameters */
 } gs_gaussians;
 
 /* One output request. tile and batch are launch parameters (0 = defaults);

@@ -29,11 +29,18 @@ EXPORTS = ("gs_workspace_size", "gs_count_pairs", "gs_render_fwd", "gs_render_bw
            "gs_probe_peaks")
 
 
+class GsHead(ctypes.Structure):
+    _fields_ = [("sigma_lo", ctypes.c_float), ("sigma_span", ctypes.c_float),
+                ("rho_scale", ctypes.c_float), ("offset_scale", ctypes.c_float),
+                ("offset_tanh", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
 class GsGaussians(ctypes.Structure):
     _fields_ = [("offset", ctypes.c_void_p), ("sigma", ctypes.c_void_p),
                 ("rho", ctypes.c_void_p), ("rgb", ctypes.c_void_p),
                 ("alpha", ctypes.c_void_p), ("n", ctypes.c_int64),
-                ("dtype", ctypes.c_int32), ("ref_grid_m", ctypes.c_int32)]
+                ("dtype", ctypes.c_int32), ("ref_grid_m", ctypes.c_int32),
+                ("head", ctypes.POINTER(GsHead))]
 
 
 class GsView(ctypes.Structure):

@@ -172,6 +172,15 @@ gs_status validate(int32_t n_images, const gs_gaussians* g, const gs_view* v, Pr
       return fail(GS_ERR_INVALID, "image %lld: n != m * lr_h * lr_w", (long long)i);
     if (G.n > 0 && (!G.offset || !G.sigma || !G.rho || !G.rgb || !G.alpha))
       return fail(GS_ERR_INVALID, "image %lld: null parameter pointer", (long long)i);
+    if (G.head) {
+      const gs_head& Hd = *G.head;
+      if (!(Hd.sigma_span > 0.0f) || !(Hd.sigma_lo >= 0.0f) || !std::isfinite(Hd.sigma_span) ||
+          !std::isfinite(Hd.sigma_lo) || !(std::fabs(Hd.rho_scale) <= 1.0f) ||
+          !std::isfinite(Hd.offset_scale) || (Hd.offset_tanh != 0 && Hd.offset_tanh != 1) ||
+          Hd.reserved[0] || Hd.reserved[1] || Hd.reserved[2])
+        return fail(GS_ERR_INVALID, "image %lld: invalid head (sigma_lo >= 0, sigma_span > 0, "
+                    "|rho_scale| <= 1, offset_tanh 0 or 1, reserved 0)", (long long)i);
+    }
     const int t = P->tile;
     const int64_t tx = (V.out_w + t - 1) / t, ty = (V.out_h + t - 1) / t;
     P->n += G.n;
@@ -297,7 +306,15 @@ gs_status upload_images(const Call& c, const gs_gaussians* g, const gs_view* v, 
       d.trunc_k = v[i].trunc_k;
       d.flags = (v[i].norm == GS_NORM_PEAK ? kFlagPeak : 0) |
                 (v[i].window == GS_WINDOW_RATIO ? kFlagRatio : 0) |
-                (v[i].align == GS_ALIGN_HALF ? kFlagHalf : 0);
+                (v[i].align == GS_ALIGN_HALF ? kFlagHalf : 0) |
+                (g[i].head ? kFlagHead : 0) |
+                (g[i].head && g[i].head->offset_tanh ? kFlagOffsetTanh : 0);
+      if (g[i].head) {
+        d.h_sigma_lo = g[i].head->sigma_lo;
+        d.h_sigma_span = g[i].head->sigma_span;
+        d.h_rho_scale = g[i].head->rho_scale;
+        d.h_offset_scale = g[i].head->offset_scale;
+      }
       d.tiles_x = (v[i].out_w + tile - 1) / tile;
       d.tiles_y = (v[i].out_h + tile - 1) / tile;
       d.t_base = tbase;

@@ -31,12 +31,19 @@ struct ImageDesc {
   int32_t dtype, m, lr_h, lr_w, out_h, out_w;
   float scale, trunc_k;
   int32_t flags, tiles_x, tiles_y, t_base;  // t_base: first global tile index
+  // fused head (kFlagHead): sigma = h_sigma_lo + h_sigma_span sigmoid(raw),
+  // rho = h_rho_scale tanh(raw), c = alpha = sigmoid(raw),
+  // o = h_offset_scale raw (or tanh(raw) with kFlagOffsetTanh)
+  float h_sigma_lo, h_sigma_span, h_rho_scale, h_offset_scale;
+  int32_t pad_[4];
 };
 // ImageDesc::flags
 constexpr int32_t kFlagPeak = 1;   // Z = 1 instead of Eq. 2's normalisation
 constexpr int32_t kFlagRatio = 2;  // Algorithm 1's ratio window instead of the k-sigma box
 constexpr int32_t kFlagHalf = 4;   // HR pixel x samples (x + 1/2)/s - 1/2
-static_assert(sizeof(ImageDesc) == 128, "ImageDesc layout");
+constexpr int32_t kFlagHead = 8;   // the parameter arrays hold raw head outputs
+constexpr int32_t kFlagOffsetTanh = 16;
+static_assert(sizeof(ImageDesc) == 160, "ImageDesc layout");
 
 struct SetupChunk {
   int32_t first, count, reset, reset_ext;   // reset: header (first chunk); reset_ext: reaches
@@ -106,6 +113,36 @@ __device__ __forceinline__ float ex2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
+}
+
+// e^x in float32 by Cody-Waite range reduction: x = n ln2 + r with ln 2 split
+// into 0.693359375 (9 bits, so n * it is exact) and -2.12194442e-4, then the
+// degree-7 Taylor polynomial of e^r (|r| <= ln2/2) in Horner form and the exact
+// scaling by 2^n. Each operation rounds to nearest and none is fused, so the
+// result is a fixed function of x (a few ulp from e^x): the fused head's window
+// edges depend on it and must be reproducible.
+__device__ __forceinline__ float exp_seq(float x) {
+  x = fminf(fmaxf(x, -87.0f), 88.0f);
+  const float n = rintf(__fmul_rn(x, 1.44269502162933349609375f));
+  const float r = __fsub_rn(__fsub_rn(x, __fmul_rn(n, 0.693359375f)),
+                            __fmul_rn(n, -2.12194441701285541057586669921875e-4f));
+  float p = 1.9841270113829523324966431e-4f;
+  p = __fadd_rn(__fmul_rn(p, r), 1.3888889225199818611145020e-3f);
+  p = __fadd_rn(__fmul_rn(p, r), 8.3333337679505348205566406e-3f);
+  p = __fadd_rn(__fmul_rn(p, r), 4.1666667908430099487304688e-2f);
+  p = __fadd_rn(__fmul_rn(p, r), 0.16666667163372039794921875f);
+  p = __fadd_rn(__fmul_rn(p, r), 0.5f);
+  p = __fadd_rn(__fmul_rn(p, r), 1.0f);
+  p = __fadd_rn(__fmul_rn(p, r), 1.0f);
+  return ldexpf(p, (int)n);
+}
+__device__ __forceinline__ float sigmoid_seq(float x) {
+  return __fdiv_rn(1.0f, __fadd_rn(1.0f, exp_seq(-x)));
+}
+__device__ __forceinline__ float tanh_seq(float x) {
+  const float e = exp_seq(__fmul_rn(-2.0f, fabsf(x)));
+  const float t = __fdiv_rn(__fsub_rn(1.0f, e), __fadd_rn(1.0f, e));
+  return x < 0.0f ? -t : t;
 }
 
 __device__ __forceinline__ float load_param(const void* p, int64_t i, int dtype) {

@@ -2,6 +2,8 @@
 //   k_setup           copies the image table into the workspace, resets counters
 //   k_preprocess      footprint pass: parameters -> record, window R_i, tile count
 //   k_preprocess_bwd  record-space gradient moments -> parameter gradients
+// Both read the parameters through load_gaussian, which applies the fused
+// Gaussian head (Sec. 3.2) when the arrays hold raw head outputs.
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -52,6 +54,75 @@ __device__ __forceinline__ void window_axis(float c, float sig, int lr_extent, f
   hi = (int)fhi;
 }
 
+// One Gaussian's parameters, physical: read as stored, or mapped from raw head
+// outputs (Sec. 3.2, Gaussian Primary Head) when the image has a fused head.
+// raw[] keeps the stored values for the head's derivatives.
+struct Phys {
+  float ox, oy, sx, sy, rho, cr, cg, cb, al;
+  float D;   // (1 - rho)(1 + rho), formed without cancellation as |rho| -> 1
+};
+
+__device__ __forceinline__ Phys load_gaussian(const ImageDesc& D, int64_t li, float (&raw)[9]) {
+  const int dt = D.dtype;
+  raw[0] = load_param(D.off, 2 * li, dt);
+  raw[1] = load_param(D.off, 2 * li + 1, dt);
+  raw[2] = load_param(D.sig, 2 * li, dt);
+  raw[3] = load_param(D.sig, 2 * li + 1, dt);
+  raw[4] = load_param(D.rho, li, dt);
+  raw[5] = load_param(D.rgb, 3 * li, dt);
+  raw[6] = load_param(D.rgb, 3 * li + 1, dt);
+  raw[7] = load_param(D.rgb, 3 * li + 2, dt);
+  raw[8] = load_param(D.alpha, li, dt);
+  Phys p;
+  if (D.flags & kFlagHead) {
+    const bool ot = (D.flags & kFlagOffsetTanh) != 0;
+    p.ox = __fmul_rn(D.h_offset_scale, ot ? tanh_seq(raw[0]) : raw[0]);
+    p.oy = __fmul_rn(D.h_offset_scale, ot ? tanh_seq(raw[1]) : raw[1]);
+    p.sx = __fadd_rn(D.h_sigma_lo, __fmul_rn(D.h_sigma_span, sigmoid_seq(raw[2])));
+    p.sy = __fadd_rn(D.h_sigma_lo, __fmul_rn(D.h_sigma_span, sigmoid_seq(raw[3])));
+    // rho = k tanh(x); 1 - rho^2 = (1 - k^2) + k^2 sech^2(x) with
+    // sech^2(x) = 4 e / (1 + e)^2, e = exp(-2|x|): no cancellation near |rho| = 1
+    {
+      const float e = exp_seq(__fmul_rn(-2.0f, fabsf(raw[4])));
+      const float t = __fdiv_rn(__fsub_rn(1.0f, e), __fadd_rn(1.0f, e));
+      const float k = D.h_rho_scale;
+      const float ope = __fadd_rn(1.0f, e);
+      const float sech2 = __fdiv_rn(4.0f * e, __fmul_rn(ope, ope));
+      p.rho = k * (raw[4] < 0.0f ? -t : t);
+      p.D = fmaf(k * k, sech2, (1.0f - k) * (1.0f + k));
+    }
+    p.cr = sigmoid_seq(raw[5]);
+    p.cg = sigmoid_seq(raw[6]);
+    p.cb = sigmoid_seq(raw[7]);
+    p.al = sigmoid_seq(raw[8]);
+  } else {
+    p.ox = raw[0]; p.oy = raw[1]; p.sx = raw[2]; p.sy = raw[3]; p.rho = raw[4];
+    p.cr = raw[5]; p.cg = raw[6]; p.cb = raw[7]; p.al = raw[8];
+    p.D = __fmul_rn(__fsub_rn(1.0f, p.rho), __fadd_rn(1.0f, p.rho));
+  }
+  return p;
+}
+
+// d(physical)/d(raw) of the fused head, in the gradient order
+// (o_x, o_y, sigma_x, sigma_y, rho, r, g, b, alpha).
+__device__ __forceinline__ void head_jacobian(const ImageDesc& D, const float (&raw)[9], const Phys& p,
+                                              float (&J)[9]) {
+  const bool ot = (D.flags & kFlagOffsetTanh) != 0;
+  for (int k = 0; k < 2; ++k) {
+    const float t = ot ? tanh_seq(raw[k]) : 0.0f;
+    J[k] = ot ? D.h_offset_scale * (1.0f - t * t) : D.h_offset_scale;
+    const float sv = sigmoid_seq(raw[2 + k]);
+    J[2 + k] = D.h_sigma_span * sv * (1.0f - sv);
+  }
+  const float e = exp_seq(__fmul_rn(-2.0f, fabsf(raw[4])));
+  const float ope = __fadd_rn(1.0f, e);
+  J[4] = D.h_rho_scale * __fdiv_rn(4.0f * e, __fmul_rn(ope, ope));   // k sech^2(x)
+  J[5] = p.cr * (1.0f - p.cr);
+  J[6] = p.cg * (1.0f - p.cg);
+  J[7] = p.cb * (1.0f - p.cb);
+  J[8] = p.al * (1.0f - p.al);
+}
+
 __device__ __forceinline__ int grid_root(int m) { return m == 1 ? 1 : m == 4 ? 2 : m == 9 ? 3 : 4; }
 
 __global__ void __launch_bounds__(kFootprintBlock) k_preprocess(Ws w) {
@@ -71,16 +142,13 @@ __global__ void __launch_bounds__(kFootprintBlock) k_preprocess(Ws w) {
     const int im = image_of_gaussian(w.images, w.n_images, gi);
     const ImageDesc& D = w.images[im];
     const int64_t li = gi - D.g_base;
-    const int dt = D.dtype;
-    const float ox = load_param(D.off, 2 * li, dt), oy = load_param(D.off, 2 * li + 1, dt);
-    const float sx = load_param(D.sig, 2 * li, dt), sy = load_param(D.sig, 2 * li + 1, dt);
-    const float rho = load_param(D.rho, li, dt);
-    const float cr = load_param(D.rgb, 3 * li, dt), cg = load_param(D.rgb, 3 * li + 1, dt),
-                cb = load_param(D.rgb, 3 * li + 2, dt);
-    const float al = load_param(D.alpha, li, dt);
+    float raw[9];
+    const Phys P = load_gaussian(D, li, raw);
+    const float ox = P.ox, oy = P.oy, sx = P.sx, sy = P.sy, rho = P.rho;
+    const float cr = P.cr, cg = P.cg, cb = P.cb, al = P.al;
     const bool ok = isfinite(ox) && isfinite(oy) && isfinite(cr) && isfinite(cg) && isfinite(cb) &&
                     isfinite(al) && sx > 0.0f && sy > 0.0f && isfinite(sx) && isfinite(sy) &&
-                    rho > -1.0f && rho < 1.0f;
+                    rho >= -1.0f && rho <= 1.0f && P.D > 0.0f && isfinite(P.D);
     const float s = D.scale;
 
     // Reference position p (float32) and the two centres: mu32 = fl(p + o) for
@@ -148,7 +216,7 @@ __global__ void __launch_bounds__(kFootprintBlock) k_preprocess(Ws w) {
     //   e = -(sA X - sK Y)^2 + g Y^2 + l,
     //   sA = r / (s sx), sK = rho r / (s sy), r = sqrt(log2(e) / (2 D)),
     //   g = -log2(e) / (2 s^2 sy^2)   (the Y marginal),  D = (1 - rho)(1 + rho).
-    const float Dr = __fmul_rn(__fsub_rn(1.0f, rho), __fadd_rn(1.0f, rho));
+    const float Dr = P.D;
     const float isx = __frcp_rn(__fmul_rn(s, sx)), isy = __frcp_rn(__fmul_rn(s, sy));
     const float r = sqrtf(__fdiv_rn(0.5f * kLog2E, Dr));
     const float sA = r * isx;
@@ -265,14 +333,12 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(Ws w) {
     for (int k = 0; k < 9; ++k) out[k] = 0.0f;
     return;
   }
-  const int dt = D.dtype;
-  const float sx = load_param(D.sig, 2 * li, dt), sy = load_param(D.sig, 2 * li + 1, dt);
-  const float rho = load_param(D.rho, li, dt);
-  const float cr = load_param(D.rgb, 3 * li, dt), cg = load_param(D.rgb, 3 * li + 1, dt),
-              cb = load_param(D.rgb, 3 * li + 2, dt);
-  const float al = load_param(D.alpha, li, dt);
+  float raw[9];
+  const Phys P = load_gaussian(D, li, raw);
+  const float sx = P.sx, sy = P.sy, rho = P.rho;
+  const float cr = P.cr, cg = P.cg, cb = P.cb, al = P.al;
   const float s = D.scale;
-  const float Dr = __fmul_rn(__fsub_rn(1.0f, rho), __fadd_rn(1.0f, rho));
+  const float Dr = P.D;
   const float isx = __frcp_rn(__fmul_rn(s, sx)), isy = __frcp_rn(__fmul_rn(s, sy));
   const float q = __fdiv_rn(kLog2E, Dr);
   const float A = -0.5f * q * isx * isx;
@@ -293,15 +359,14 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(Ws w) {
   const float drho = kLn2 * two_r_over_D * (A * SXX + C * SYY) +
                      SXY * (1.0f + rho * rho) / (s * s * sx * sy * Dr * Dr) +
                      dens * S0 * rho / Dr;
-  out[0] = s * dcx;
-  out[1] = s * dcy;
-  out[2] = dsx;
-  out[3] = dsy;
-  out[4] = drho;
-  out[5] = al * Cr;
-  out[6] = al * Cg;
-  out[7] = al * Cb;
-  out[8] = cr * Cr + cg * Cg + cb * Cb;
+  float gr[9] = {s * dcx, s * dcy, dsx, dsy, drho, al * Cr, al * Cg, al * Cb,
+                 cr * Cr + cg * Cg + cb * Cb};
+  if (D.flags & kFlagHead) {   // chain rule through the head's activations
+    float J[9];
+    head_jacobian(D, raw, P, J);
+    for (int k = 0; k < 9; ++k) gr[k] *= J[k];
+  }
+  for (int k = 0; k < 9; ++k) out[k] = gr[k];
 }
 
 }  // namespace

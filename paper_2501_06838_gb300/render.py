@@ -11,7 +11,10 @@ its adjoint runs in the library's CUDA kernels (include/gs.h). Functions:
 
 Parameters are physical (post-activation): offset o (or absolute centre when
 ref_grid_m == 0), sigma, rho, rgb, alpha, all in LR pixels (GSASR, arXiv
-2501.06838, Sec. 3.1-3.2), stored as float32, bfloat16 or float16.
+2501.06838, Sec. 3.1-3.2), stored as float32, bfloat16 or float16 -- or raw
+outputs of the Gaussian primary head when `Gaussians.head` is set (the
+library applies the head's activations and returns gradients for the raw
+values).
 """
 from __future__ import annotations
 
@@ -35,6 +38,7 @@ class Gaussians:
     rgb: torch.Tensor     # [N, 3]
     alpha: torch.Tensor   # [N]
     ref_grid_m: int = 1
+    head: object = None   # fused head (sigma_lo, sigma_span, rho_scale, offset_scale, offset_tanh)
 
     @property
     def n(self) -> int:
@@ -64,8 +68,15 @@ def _struct_g(g: Gaussians) -> _abi.GsGaussians:
             raise ValueError("parameter tensors must be CUDA tensors")
         if not t.is_contiguous() or tuple(t.shape) != shp:
             raise ValueError(f"parameter tensor must be contiguous with shape {shp}, got {tuple(t.shape)}")
-    return _abi.GsGaussians(ts[0].data_ptr(), ts[1].data_ptr(), ts[2].data_ptr(),
-                            ts[3].data_ptr(), ts[4].data_ptr(), n, _DTYPES[dt], int(g.ref_grid_m))
+    hp = None
+    if g.head is not None:
+        h = g.head
+        hp = ctypes.pointer(_abi.GsHead(float(h.sigma_lo), float(h.sigma_span), float(h.rho_scale),
+                                        float(h.offset_scale), int(h.offset_tanh)))
+    G = _abi.GsGaussians(ts[0].data_ptr(), ts[1].data_ptr(), ts[2].data_ptr(),
+                         ts[3].data_ptr(), ts[4].data_ptr(), n, _DTYPES[dt], int(g.ref_grid_m), hp)
+    G._head_keep = hp   # the C struct points into this object during the call
+    return G
 
 
 def _struct_v(v, tile: int = 0, batch: int = 0, adjoint: int = 0) -> _abi.GsView:
@@ -82,7 +93,9 @@ def _arrays(gs: Sequence[Gaussians], views, tile=0, batch=0):
     n = len(gs)
     if n != len(views) or n == 0:
         raise ValueError("need one view per image and at least one image")
-    G = (_abi.GsGaussians * n)(*[_struct_g(g) for g in gs])
+    structs = [_struct_g(g) for g in gs]
+    G = (_abi.GsGaussians * n)(*structs)
+    G._head_keep = [st._head_keep for st in structs]   # head structs the array points to
     V = (_abi.GsView * n)(*[_struct_v(v, tile, batch) for v in views])
     return n, G, V
 
@@ -234,10 +247,13 @@ def _split_grads(gr: torch.Tensor, dtype):
 
 
 class GSRender(torch.autograd.Function):
+    """apply(offset, sigma, rho, rgb, alpha, view[, ref_grid_m[, head]]): with a
+    head the five tensors are raw head outputs and their gradients are too."""
+
     @staticmethod
-    def forward(ctx, offset, sigma, rho, rgb, alpha, view, ref_grid_m: int = 1):
+    def forward(ctx, offset, sigma, rho, rgb, alpha, view, ref_grid_m: int = 1, head=None):
         g = Gaussians(offset.contiguous(), sigma.contiguous(), rho.contiguous(), rgb.contiguous(),
-                      alpha.contiguous(), ref_grid_m)
+                      alpha.contiguous(), ref_grid_m, head)
         out, ws = render(g, view)
         ctx.g, ctx.view, ctx.ws = g, view, ws
         return out
@@ -245,19 +261,22 @@ class GSRender(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_out):
         gr = render_bwd(ctx.g, ctx.view, grad_out, ctx.ws)
-        return (*_split_grads(gr, ctx.g.offset.dtype), None, None)
+        return (*_split_grads(gr, ctx.g.offset.dtype), None, None, None)
 
 
 class GSRenderBatched(torch.autograd.Function):
     """Images of uneven sizes and scales in one launch chain. Parameters are
-    concatenated over images; sizes[i] Gaussians belong to image i."""
+    concatenated over images; sizes[i] Gaussians belong to image i. With a
+    head (a fused Gaussian primary head for every image) they are raw head
+    outputs: apply(views, ref_grid_m, sizes, head, offset, sigma, rho, rgb,
+    alpha); pass head=None for physical parameters."""
 
     @staticmethod
-    def forward(ctx, views, ref_grid_m, sizes, offset, sigma, rho, rgb, alpha):
+    def forward(ctx, views, ref_grid_m, sizes, head, offset, sigma, rho, rgb, alpha):
         gs, o = [], 0
         ts = [t.contiguous() for t in (offset, sigma, rho, rgb, alpha)]
         for n in sizes:
-            gs.append(Gaussians(*[t[o:o + n] for t in ts], ref_grid_m=ref_grid_m))
+            gs.append(Gaussians(*[t[o:o + n] for t in ts], ref_grid_m=ref_grid_m, head=head))
             o += n
         outs, ws = render_batched(gs, views)
         ctx.gs, ctx.views, ctx.ws, ctx.dtype = gs, views, ws, offset.dtype
@@ -269,7 +288,7 @@ class GSRenderBatched(torch.autograd.Function):
               for g, v in zip(grad_outs, ctx.views)]
         grads = render_batched_bwd(ctx.gs, ctx.views, go, ctx.ws)
         gr = torch.cat(grads, 0)
-        return (None, None, None, *_split_grads(gr, ctx.dtype))
+        return (None, None, None, None, *_split_grads(gr, ctx.dtype))
 
 
 class Plan:

@@ -4,8 +4,9 @@ A random-init 8-block, 64-channel 3x3 convolutional encoder on 48x48 LR crops
 and a 1x1-convolution Gaussian head predict, per LR pixel, one Gaussian's
 offset, sigma, rho, colour and opacity (the head's activations follow GSASR
 Sec. 3.2, Gaussian Primary Head: tanh for rho, sigmoid for sigma, colour and
-opacity, mu = p + o). The parameters are stored in BF16 and rendered by the
-library's batched autograd Function at a per-sample scale s ~ U[1, 4]
+opacity, mu = p + o; by default they run fused inside the renderer's footprint
+pass, with their derivatives in its chain-rule pass). The raw outputs are
+stored in BF16 and rendered by the library's batched autograd Function at a per-sample scale s ~ U[1, 4]
 (training-time scales of Sec. 4.1); the L1 loss against the HR target
 (Sec. 3.2, Rendering) is back-propagated through the render's adjoint into the
 encoder. The encoder and head are plain PyTorch layers: they stand in for the
@@ -29,8 +30,16 @@ class ResBlock(nn.Module):
         return x + self.c2(torch.relu(self.c1(x)))
 
 
+class HeadSpec:
+    """The head's activations: o = tanh (|o| < 1 LR px), sigma = 0.2 + 2.8 sigmoid
+    (LR px), rho = 0.9 tanh, colour and opacity sigmoid (a gs_head)."""
+    sigma_lo, sigma_span, rho_scale, offset_scale, offset_tanh = 0.2, 2.8, 0.9, 1.0, 1
+
+
 class ToyGaussianSR(nn.Module):
-    """LR image [B, 3, H, W] -> per-pixel Gaussian parameters (m = 1)."""
+    """LR image [B, 3, H, W] -> per-pixel Gaussian parameters (m = 1): raw head
+    outputs (activated inside the renderer), or with activate=True the physical
+    parameters through PyTorch's own activations."""
 
     def __init__(self, channels: int = 64, blocks: int = 8):
         super().__init__()
@@ -38,12 +47,15 @@ class ToyGaussianSR(nn.Module):
         self.body = nn.Sequential(*[ResBlock(channels) for _ in range(blocks)])
         self.head = nn.Conv2d(channels, 9, 1)
 
-    def forward(self, lr):
+    def forward(self, lr, activate: bool = False):
         h = self.head(self.body(self.inp(lr)))           # [B, 9, H, W]
         h = h.permute(0, 2, 3, 1).reshape(lr.shape[0], -1, 9)
-        offset = torch.tanh(h[..., 0:2])                   # |o| < 1 LR px
-        sigma = 0.2 + 2.8 * torch.sigmoid(h[..., 2:4])     # LR px
-        rho = 0.9 * torch.tanh(h[..., 4])
+        if not activate:
+            return h[..., 0:2], h[..., 2:4], h[..., 4], h[..., 5:8], h[..., 8]
+        H = HeadSpec
+        offset = H.offset_scale * torch.tanh(h[..., 0:2])
+        sigma = H.sigma_lo + H.sigma_span * torch.sigmoid(h[..., 2:4])
+        rho = H.rho_scale * torch.tanh(h[..., 4])
         rgb = torch.sigmoid(h[..., 5:8])
         alpha = torch.sigmoid(h[..., 8])
         return offset, sigma, rho, rgb, alpha
@@ -54,7 +66,7 @@ class TrainStep:
     optimisation step and returns the loss (a device tensor)."""
 
     def __init__(self, size: int = 48, device="cuda", param_dtype=torch.bfloat16, lr=2e-4,
-                 norm: int = 0):
+                 norm: int = 0, fused_head: bool = True):
         torch.manual_seed(0)
         self.model = ToyGaussianSR().to(device)
         self.opt = torch.optim.Adam(self.model.parameters(), lr=lr)
@@ -62,6 +74,7 @@ class TrainStep:
         self.dtype = param_dtype
         self.norm = norm
         self.device = device
+        self.fused_head = fused_head
 
     def views(self, scales):
         from gs_synthetic import View, out_size
@@ -71,11 +84,11 @@ class TrainStep:
     def __call__(self, lr_images, targets, scales):
         views = self.views(scales)
         b = lr_images.shape[0]
-        offset, sigma, rho, rgb, alpha = self.model(lr_images)
+        offset, sigma, rho, rgb, alpha = self.model(lr_images, activate=not self.fused_head)
         n = self.size * self.size
         cast = lambda t: t.reshape((b * n,) + t.shape[2:]).to(self.dtype).contiguous()
-        outs = GSRenderBatched.apply(views, 1, [n] * b, cast(offset), cast(sigma), cast(rho),
-                                     cast(rgb), cast(alpha))
+        outs = GSRenderBatched.apply(views, 1, [n] * b, HeadSpec if self.fused_head else None,
+                                     cast(offset), cast(sigma), cast(rho), cast(rgb), cast(alpha))
         loss = sum((o - t).abs().mean() for o, t in zip(outs, targets)) / b
         self.opt.zero_grad(set_to_none=True)
         loss.backward()

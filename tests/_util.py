@@ -16,7 +16,7 @@ def device_gaussians(g: S.GaussianSet, device="cuda"):
         else:
             t = torch.from_numpy(np.ascontiguousarray(arr))
         ts.append(t.to(device).contiguous())
-    return gs.Gaussians(*ts, ref_grid_m=g.ref_grid_m)
+    return gs.Gaussians(*ts, ref_grid_m=g.ref_grid_m, head=getattr(g, "head", None))
 
 
 def normwise(a, ref, axis=None):

@@ -37,7 +37,7 @@ def test_host_only_entry_points(lib):
     assert lib.gs_status_string(2) == b"GS_ERR_CAPACITY"
     assert lib.gs_version().startswith(b"gs ")
     assert lib.gs_kernel_name(9) == b"raster_fwd"
-    G = (_abi.GsGaussians * 1)(_abi.GsGaussians(1, 1, 1, 1, 1, 2304, 0, 1))
+    G = (_abi.GsGaussians * 1)(_abi.GsGaussians(1, 1, 1, 1, 1, 2304, 0, 1, None))
     V = (_abi.GsView * 1)(_abi.GsView(48, 48, 192, 192, 4.0, 3.0, 0, 16, 64, 0, 0, 0,
                                       _abi.GS_BINNING_SORT, 0))
     a = lib.gs_workspace_size(1, G, V, 0)

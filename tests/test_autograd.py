@@ -68,7 +68,7 @@ def test_gsrender_batched_autograd():
     views = [S.View(h, w, S.out_size(h, s), S.out_size(w, s), s) for h, w, s in sizes]
     cat = [torch.cat([t for t in ts]) for ts in zip(*[device_gaussians(g).tensors() for g in gsets])]
     params = [t.clone().requires_grad_(True) for t in cat]
-    outs = gs.GSRenderBatched.apply(views, 1, [g.n for g in gsets], *params)
+    outs = gs.GSRenderBatched.apply(views, 1, [g.n for g in gsets], None, *params)
     gos = [S.grad_out(20 + i, v.out_h, v.out_w) for i, v in enumerate(views)]
     loss = sum((o * torch.from_numpy(x).cuda()).sum() for o, x in zip(outs, gos))
     loss.backward()

@@ -33,3 +33,22 @@ def test_training_steps_reduce_loss():
     # gradients reached the first encoder layer
     assert step.model.inp.weight.grad is not None
     assert float(step.model.inp.weight.grad.abs().sum()) > 0
+
+
+@pytest.mark.gpu
+def test_fused_head_matches_pytorch_activations():
+    """The renderer's fused head and the same activations in PyTorch give the same
+    first-step loss and encoder gradient (float32 parameters, same seed)."""
+    import torch
+    from paper_2501_06838_gb300.train_step import TrainStep
+    lr, hrs, scales = S.config5_batch(0)
+    lr_t = torch.from_numpy(lr).cuda()
+    hr_t = [torch.from_numpy(h).cuda() for h in hrs]
+    res = {}
+    for fused in (True, False):
+        step = TrainStep(param_dtype=torch.float32, fused_head=fused, lr=0.0)
+        loss = float(step(lr_t, hr_t, scales))
+        res[fused] = (loss, step.model.inp.weight.grad.detach().clone())
+    assert abs(res[True][0] - res[False][0]) < 1e-5 * abs(res[False][0])
+    ga, gb = res[True][1], res[False][1]
+    assert float((ga - gb).abs().max()) < 1e-3 * float(gb.abs().max())
