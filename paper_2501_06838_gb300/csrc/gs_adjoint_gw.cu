@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(kGwWarps * 32) k_raster_bwd_gw(Ws w) {
   float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   if (x0 <= x1 && y0 <= y1) {   // warp-uniform
     const ImageDesc& D = w.images[image_of_gaussian(w.images, w.n_images, gi)];
-    const float* go = D.grad_out;
+    const float* go = w.direct ? w.grad_out0 : D.grad_out;
     const int W = D.out_w;
     const int64_t plane = (int64_t)D.out_h * W;
     const bool aligned = (W & 1) == 0 && (reinterpret_cast<uintptr_t>(go) & 7) == 0;

@@ -257,7 +257,9 @@ gs_status prepare(int32_t n_images, const gs_gaussians* g, const gs_view* v, voi
   w.ext = reinterpret_cast<int4*>(b + L.ext);
   w.tcount = reinterpret_cast<uint32_t*>(b + L.tcount);
   w.grid = c->P.grid;
-  w.pad_ = 0;
+  w.direct = 0;
+  w.grad_out0 = nullptr;
+  w.grads0 = nullptr;
   w.n = c->P.n;
   w.capacity = cap;
   w.n_images = n_images;
@@ -339,15 +341,10 @@ gs_status run_forward(int32_t n_images, const gs_gaussians* g, const gs_view* v,
   if (st != GS_OK) return st;
   cudaError_t e;
   if (c.w.grid) {
-    // grid-implicit binning: the footprint pass counts pairs per tile (into a
-    // cleared array) and measures the reach; the raster enumerates each
-    // tile's candidates and leaves the tile's list for the adjoint (no sort)
-    e = cudaSuccess;
-    if (c.w.tiles > 0) {
-      LaunchScope ls(kKMemset, s);
-      e = cudaMemsetAsync(c.w.tcount, 0, 4 * (size_t)c.w.tiles, s);
-    }
-    if (e != cudaSuccess) return cuda_fail(e, "memset");
+    // grid-implicit binning: the footprint pass counts pairs per tile (into
+    // the array the setup kernel cleared) and measures the reach; the raster
+    // enumerates each tile's candidates and leaves the tile's list for the
+    // adjoint (no sort)
     e = launch_preprocess(c.w, s);
     if (e != cudaSuccess) return cuda_fail(e, "preprocess");
     e = launch_raster_fwd(c.w, nullptr, c.P.batch, s);
@@ -383,12 +380,20 @@ gs_status run_backward(int32_t n_images, const gs_gaussians* g, const gs_view* v
     if (!grad_outs[i]) return fail(GS_ERR_INVALID, "null grad_out pointer for image %lld", (long long)i);
     if (g[i].n > 0 && !grads[i]) return fail(GS_ERR_INVALID, "null grads pointer for image %lld", (long long)i);
   }
-  st = upload_images(c, g, v, nullptr, grad_outs, grads, 0, s);
-  if (st != GS_OK) return st;
+  if (n_images == 1) {
+    // the image table is the forward's; the gradient pointers go by value
+    c.w.direct = 1;
+    c.w.grad_out0 = grad_outs[0];
+    c.w.grads0 = grads[0];
+  } else {
+    st = upload_images(c, g, v, nullptr, grad_outs, grads, 0, s);
+    if (st != GS_OK) return st;
+  }
   if (c.w.n == 0) return GS_OK;
   cudaError_t e;
   if (c.P.adjoint == GS_ADJOINT_TILE) {
     {
+      // the tile adjoint adds into the record-space accumulators
       LaunchScope ls(kKMemset, s);
       e = cudaMemsetAsync(c.w.grec, 0, 48 * (size_t)c.w.n, s);
       if (e != cudaSuccess) return cuda_fail(e, "memset");

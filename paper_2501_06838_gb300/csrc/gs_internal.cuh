@@ -102,7 +102,9 @@ struct Ws {
   int32_t sort_blocks;
   int32_t scan_parts;         // size of `parts`
   int32_t grid;               // 1: grid-implicit binning (no pair list), 0: sorted pair list
-  int32_t pad_;
+  int32_t direct;             // 1: one image, its grad_out / grads pointers below (adjoint)
+  const float* grad_out0;     // direct: dL/dI of image 0
+  float* grads0;              // direct: parameter gradients of image 0
 };
 
 // ---------------------------------------------------------------------------

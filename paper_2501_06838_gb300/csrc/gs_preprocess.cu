@@ -4,6 +4,8 @@
 //   k_preprocess_bwd  record-space gradient moments -> parameter gradients
 // Both read the parameters through load_gaussian, which applies the fused
 // Gaussian head (Sec. 3.2) when the arrays hold raw head outputs.
+#include <algorithm>
+
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -15,7 +17,11 @@ constexpr float kLn2 = 0.6931471805599453f;
 constexpr float kLog2TwoPi = 2.6514961294723187f;
 
 __global__ void k_setup(SetupChunk c, Ws w) {
-  int t = threadIdx.x;
+  const int t = threadIdx.x;
+  if (c.reset && w.grid)   // clear the per-tile pair counts of grid binning
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + t; i < w.tiles; i += (int64_t)gridDim.x * blockDim.x)
+      w.tcount[i] = 0u;
+  if (blockIdx.x != 0) return;
   if (t < c.count) w.images[c.first + t] = c.d[t];
   if (t < c.count && c.reset_ext) w.ext[c.first + t] = make_int4(0, 0, 0, 0);
   if (c.reset && t == 0) {
@@ -324,7 +330,7 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(Ws w) {
   const int im = image_of_gaussian(w.images, w.n_images, gi);
   const ImageDesc& D = w.images[im];
   const int64_t li = gi - D.g_base;
-  float* out = D.grads + li * 9;
+  float* out = (w.direct ? w.grads0 : D.grads) + li * 9;
   const float4* rec = w.records + gi * kRecordF4;
   const float4 r3 = rec[3];
   const bool live = __float_as_int(r3.x) <= __float_as_int(r3.y) &&
@@ -344,9 +350,10 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(Ws w) {
   const float A = -0.5f * q * isx * isx;
   const float B = q * rho * isx * isy;
   const float C = -0.5f * q * isy * isy;
-  const float* m = w.grec + gi * 12;
-  const float SX = m[0], SY = m[1], SXX = m[2], SXY = m[3], SYY = m[4];
-  const float Cr = m[5], Cg = m[6], Cb = m[7];
+  const float4* gm = reinterpret_cast<const float4*>(w.grec + gi * 12);
+  const float4 m0 = gm[0], m1 = gm[1];
+  const float SX = m0.x, SY = m0.y, SXX = m0.z, SXY = m0.w, SYY = m1.x;
+  const float Cr = m1.y, Cg = m1.z, Cb = m1.w;
   const float4 rc = rec[2];
   const float S0 = fmaf(rc.z, Cb, fmaf(rc.y, Cg, rc.x * Cr));
 
@@ -373,7 +380,9 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(Ws w) {
 
 cudaError_t launch_setup(const SetupChunk& c, const Ws& w, cudaStream_t s) {
   LaunchScope ls(kKSetup, s);
-  k_setup<<<1, 32, 0, s>>>(c, w);
+  int blocks = 1;
+  if (c.reset && w.grid) blocks = (int)std::min<int64_t>(1024, std::max<int64_t>(1, ((int64_t)w.tiles + 255) / 256));
+  k_setup<<<blocks, 256, 0, s>>>(c, w);
   return cudaGetLastError();
 }
 

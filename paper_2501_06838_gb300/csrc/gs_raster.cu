@@ -499,9 +499,10 @@ __global__ void __launch_bounds__(TILE * TILE / BY) k_raster_bwd(Ws w, const uin
       const bool in = x < W && y < H;
       const int64_t o = (int64_t)y * W + x;
       float* gk = reinterpret_cast<float*>(&g[k / 2][0]) + (k & 1);
-      gk[0] = in ? __ldg(D->grad_out + o) : 0.0f;
-      gk[2] = in ? __ldg(D->grad_out + plane + o) : 0.0f;
-      gk[4] = in ? __ldg(D->grad_out + 2 * plane + o) : 0.0f;
+      const float* go = w.direct ? w.grad_out0 : D->grad_out;
+      gk[0] = in ? __ldg(go + o) : 0.0f;
+      gk[2] = in ? __ldg(go + plane + o) : 0.0f;
+      gk[4] = in ? __ldg(go + 2 * plane + o) : 0.0f;
     }
   }
 
