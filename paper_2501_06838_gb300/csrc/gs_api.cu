@@ -341,10 +341,10 @@ gs_status run_forward(int32_t n_images, const gs_gaussians* g, const gs_view* v,
   if (st != GS_OK) return st;
   cudaError_t e;
   if (c.w.grid) {
-    // grid-implicit binning: the footprint pass counts pairs per tile (into
-    // the array the setup kernel cleared) and measures the reach; the raster
-    // enumerates each tile's candidates and leaves the tile's list for the
-    // adjoint (no sort)
+    // grid-implicit binning: the footprint pass records per-row differences of
+    // the pairs per tile (into the array the setup kernel cleared) and the
+    // reach; the raster sums its tile's count, enumerates the tile's
+    // candidates and leaves the tile's list for the adjoint (no sort)
     e = launch_preprocess(c.w, s);
     if (e != cudaSuccess) return cuda_fail(e, "preprocess");
     e = launch_raster_fwd(c.w, nullptr, c.P.batch, s);

@@ -92,7 +92,8 @@ struct Ws {
   float* grec;                // [N][12] record-space gradient moments
   short4* win;                // [N] windows (x0, x1, y0, y1) for grid binning (empty: never meets a tile)
   int4* ext;                  // [n_images] reach (DL, DR, DT, DB) of the windows past their LR cell, HR px
-  uint32_t* tcount;           // [T] grid mode: (tile, Gaussian) pairs per tile
+  uint32_t* tcount;           // [T] grid mode: per-row differences of the (tile, Gaussian)
+                              // pairs per tile (a tile's count is the prefix along its row)
   int64_t n;                  // total Gaussians
   int64_t capacity;           // pair capacity
   int32_t n_images;

@@ -144,6 +144,7 @@ __global__ void __launch_bounds__(kFootprintBlock) k_preprocess(Ws w) {
   int4 reach = make_int4(0, 0, 0, 0);   // grid mode: window reach past the LR cell
   int rim = -1;                          // image of `reach` (-1: none)
   uint4 trk = make_uint4(0u, 0u, 0u, 0u);  // tile rectangle, for the per-tile counts
+  uint32_t tcol0 = 0u;                     // its first tile column in the image
   if (gi < w.n) {
     const int im = image_of_gaussian(w.images, w.n_images, gi);
     const ImageDesc& D = w.images[im];
@@ -261,6 +262,7 @@ __global__ void __launch_bounds__(kFootprintBlock) k_preprocess(Ws w) {
       const uint32_t tw = (uint32_t)(tx1 - tx0 + 1), th = (uint32_t)(ty1 - ty0 + 1);
       cnt = tw * th;
       tr = make_uint4((uint32_t)(D.t_base + ty0 * D.tiles_x + tx0), (uint32_t)D.tiles_x, tw, th);
+      tcol0 = (uint32_t)tx0;
       pix = (unsigned long long)(x1 - x0 + 1) * (unsigned long long)(y1 - y0 + 1);
     }
     w.trect[gi] = tr;
@@ -277,18 +279,24 @@ __global__ void __launch_bounds__(kFootprintBlock) k_preprocess(Ws w) {
     unsigned long long c64 = cnt;
     for (int o = 16; o > 0; o >>= 1) c64 += __shfl_xor_sync(0xffffffffu, c64, o);
     if ((threadIdx.x & 31) == 0 && c64) atomicAdd(&w.hdr->pairs, c64);
-    // pairs per tile: each lane walks its tile rectangle; lanes on the same
-    // tile in the same step add together (one atomic per tile and step)
+    // pairs per tile, as per-row differences: +1 at the rectangle's first
+    // tile of each of its rows, -1 just past its last (a tile's count is the
+    // sum along its row up to it; the raster forms it). Lanes on the same entry in the same step add
+    // together: one atomic per entry and step.
     {
       const int lane = threadIdx.x & 31;
-      int kx = 0, ky = 0;
+      const uint32_t rows = cnt ? trk.w : 0u;
+      const uint32_t last = tcol0 + trk.z;   // column just past the rectangle
       for (uint32_t k = 0;; ++k) {
-        const bool act = k < cnt;
+        const bool act = k < rows;
         if (!__any_sync(0xffffffffu, act)) break;
-        const uint32_t t = act ? trk.x + (uint32_t)ky * trk.y + (uint32_t)kx : 0xffffffffu;
-        const unsigned grp = __match_any_sync(0xffffffffu, t);
-        if (act && (__ffs(grp) - 1) == lane) atomicAdd(w.tcount + t, (uint32_t)__popc(grp));
-        if (act && ++kx == (int)trk.z) { kx = 0; ++ky; }
+        const uint32_t a = act ? trk.x + k * trk.y : 0xffffffffu;
+        const unsigned ga = __match_any_sync(0xffffffffu, a);
+        if (act && (__ffs(ga) - 1) == lane) atomicAdd(w.tcount + a, (uint32_t)__popc(ga));
+        const bool endin = act && last < trk.y;
+        const uint32_t b = endin ? a + trk.z : 0xffffffffu;
+        const unsigned gb = __match_any_sync(0xffffffffu, b);
+        if (endin && (__ffs(gb) - 1) == lane) atomicSub(w.tcount + b, (uint32_t)__popc(gb));
       }
     }
     const int im0 = __shfl_sync(0xffffffffu, rim, 0);

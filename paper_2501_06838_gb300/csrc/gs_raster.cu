@@ -299,7 +299,19 @@ __global__ void __launch_bounds__(TILE * TILE / BY) k_raster_fwd(Ws w, const uin
   bool lok = false;
   if constexpr (GRID) {
     grid_source_init<TILE, NT, PF>(w, D, ox, oy, qbuf, src);
-    lcount = (int)w.tcount[blockIdx.x];
+    {
+      // the tile's pair count: the prefix, along its tile row, of the
+      // footprint pass's per-row differences
+      const int lane = threadIdx.x & 31;
+      const int lt = blockIdx.x - D->t_base;
+      const int tyl = lt / D->tiles_x, txl = lt - tyl * D->tiles_x;
+      const uint32_t* row = w.tcount + D->t_base + (int64_t)tyl * D->tiles_x;
+      uint32_t acc = 0u;
+      for (int x = lane; x <= txl; x += 32) acc += row[x];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      lcount = (int)acc;
+    }
     if (threadIdx.x == 0) {
       const unsigned long long b = atomicAdd(&w.hdr->list_cursor, (unsigned long long)lcount);
       const bool fits = b + (unsigned long long)lcount <= (unsigned long long)w.capacity;
