@@ -263,6 +263,15 @@ def run_gpu(args, rank, world, local_rank):
         return gs.Gaussians(*ts, ref_grid_m=g.ref_grid_m)
 
     dgs = [dev_g(g) for g in gsets]
+    tuned = None
+    if args.tune or (args.tune is None and args.workload in ("c3",) and not args.tile):
+        # the launch parameters the library's autotuner picks for this workload
+        import importlib
+        T = importlib.import_module("paper_2501_06838_gb300.tune")
+        tuned = T.tune(dgs, views, with_grads=with_adj, reps=3)
+        args.tile, args.batch = tuned["tile"], tuned["batch"]
+        for v in views:
+            v.binning = tuned["binning_code"]
     plan = gs.Plan(dgs, views, tile=args.tile, batch=args.batch, with_grads=with_adj)
     if with_adj:
         for i, v in enumerate(views):
@@ -379,6 +388,9 @@ def run_gpu(args, rank, world, local_rank):
                    "l2": "flushed before every step (256 MiB write, outside the timed events)",
                    "tile": plan.V[0].tile or 16, "smem_batch": plan.V[0].batch or 32,
                    "binning": binning_desc(plan.V[0].binning, gsets, views),
+                   "autotuned": None if tuned is None else {k: tuned[k] for k in
+                                                           ("tile", "batch", "binning", "ms",
+                                                            "from_cache", "n_timed")},
                    "adjoint": "gaussian-warp" if plan.V[0].adjoint == 2 else "tile",
                    "hr_pixels_per_step": hr_pix, "gaussians": sum(g.n for g in dgs),
                    "parallelism": f"replicas x{world} (one full workload per GPU)"},
@@ -652,6 +664,10 @@ def main():
                     help="adjoint kernel: per-tile with atomics, or one warp per Gaussian")
     ap.add_argument("--binning", choices=["auto", "sort", "grid"], default=None,
                     help="per-tile Gaussian lists: radix-sorted pairs or grid-implicit")
+    ap.add_argument("--tune", dest="tune", action="store_true", default=None,
+                    help="pick tile / batch / binning with the library's autotuner "
+                         "(default for the c3 workload)")
+    ap.add_argument("--no-tune", dest="tune", action="store_false")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-probe", action="store_true", help="skip the unit-throughput probe")

@@ -290,6 +290,38 @@ typedef struct gs_peaks {
  * Not part of the method: it supplies the ALU roofline's denominators. */
 gs_status gs_probe_peaks(void* scratch, size_t scratch_bytes, void* stream, gs_peaks* out);
 
+/* Launch parameters picked by gs_tune for one workload. */
+typedef struct gs_tuning {
+  int32_t tile, batch, binning, adjoint;  /* values for the gs_view fields of the same names */
+  float ms;                               /* median time of one call (forward + adjoint if timed) */
+  int32_t from_cache;                     /* 1: read from the cache file, nothing was timed */
+  int32_t n_timed;                        /* candidates timed */
+  int32_t reserved;
+} gs_tuning;
+
+/* Autotuner for the launch parameters (not part of the method: they change the
+ * speed, not the result). Times the render of these images, forward and, when
+ * grad_outs and grads are non-NULL, the adjoint, on `stream` for each
+ * candidate: tile 16, 8 and 32 with batch 32 and 64 (64 and 128 at tile 32),
+ * each with SORT binning and, where it applies, GRID binning; adjoint TILE.
+ * Every candidate runs twice untimed, then `reps` times (1..100) between CUDA
+ * events; the median decides. The fastest is returned in *best (host). A
+ * candidate whose pairs do not fit the workspace is skipped: size `ws` with
+ * gs_workspace_size(..., cap) for cap = gs_count_pairs at tile 8 (the most
+ * pairs). outs / grads are overwritten by the timed calls. Synchronous.
+ *
+ * cache_path (may be NULL): a text file of lines
+ *   "<signature> <tile> <batch> <binning> <adjoint> <ms>",
+ * the signature being the device name, parameter dtype, fwd or fwd+bwd, and
+ * the log2 size classes of the HR pixels, the images and the pairs per pixel.
+ * A matching line is returned without timing (from_cache = 1); a new result is
+ * appended. g, v, outs, grad_outs, grads: as for gs_render_batched /
+ * gs_render_batched_bwd (the views' own tile, batch, binning and adjoint are
+ * ignored). */
+gs_status gs_tune(int32_t n_images, const gs_gaussians* g, const gs_view* v, float* const* outs,
+                  const float* const* grad_outs, float* const* grads, void* ws, size_t ws_bytes,
+                  void* stream, int32_t reps, const char* cache_path, gs_tuning* best);
+
 /* Library build identity, e.g. "gs 0.1 sm_103a". */
 const char* gs_version(void);
 

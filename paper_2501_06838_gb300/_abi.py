@@ -26,7 +26,7 @@ EXPORTS = ("gs_workspace_size", "gs_count_pairs", "gs_render_fwd", "gs_render_bw
            "gs_render_batched", "gs_render_batched_bwd", "gs_sync_status", "gs_read_stats",
            "gs_last_error", "gs_status_string", "gs_launch_count", "gs_timing_enable",
            "gs_timing_read", "gs_kernel_name", "gs_version", "gs_render_fwd_noalloc",
-           "gs_probe_peaks")
+           "gs_probe_peaks", "gs_tune")
 
 
 class GsHead(ctypes.Structure):
@@ -64,6 +64,12 @@ class GsPeaks(ctypes.Structure):
                 ("ex2_per_s", ctypes.c_double), ("fwd_pairs_scalar_per_s", ctypes.c_double),
                 ("fwd_pairs_packed_per_s", ctypes.c_double), ("sm_count", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
+
+
+class GsTuning(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int32), ("batch", ctypes.c_int32), ("binning", ctypes.c_int32),
+                ("adjoint", ctypes.c_int32), ("ms", ctypes.c_float), ("from_cache", ctypes.c_int32),
+                ("n_timed", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class GsError(RuntimeError):
@@ -111,6 +117,8 @@ def load(path: str | None = None):
             "gs_version": (ctypes.c_char_p, []),
             "gs_render_fwd_noalloc": (i32, [G, V, vp, vp]),
             "gs_probe_peaks": (i32, [vp, sz, vp, ctypes.POINTER(GsPeaks)]),
+            "gs_tune": (i32, [i32, G, V, fpp, fpp, fpp, vp, sz, vp, i32, ctypes.c_char_p,
+                              ctypes.POINTER(GsTuning)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)

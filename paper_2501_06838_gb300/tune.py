@@ -1,99 +1,54 @@
-"""Autotuner for the launch parameters of the render: screen tile edge
-(8, 16, 32 HR px) and Gaussians per shared-memory batch (32 or 64 per warp
-group). Each candidate is timed on the caller's own workload with CUDA events
-(median of `reps` calls after a warm-up), the fastest is returned and cached
-in a JSON file keyed by the device, the parameter dtype, whether the adjoint is
-included, and the workload's size class (log2 of HR pixels, of images and of
-tile pairs per HR pixel).
+"""Autotuner for the launch parameters of the render (screen tile edge,
+Gaussians per shared-memory batch, binning): a thin binding of the library's
+gs_tune, which times every candidate on the caller's own workload with CUDA
+events (median of `reps` calls after two warm-up calls), returns the fastest
+and keeps it in a text cache keyed by the workload's signature (device, dtype,
+fwd or fwd+bwd, and the log2 size classes of HR pixels, images and pairs per
+pixel).
 """
 from __future__ import annotations
 
-import json
-import math
+import ctypes
 import os
-import threading
 
 import torch
 
-from .render import Plan, count_pairs
+from . import _abi
+from .render import Plan, _stream
 
-CANDIDATES = ((16, 32), (16, 64), (8, 32), (8, 64), (32, 64), (32, 128))
-_lock = threading.Lock()
+_BINNING = {_abi.GS_BINNING_SORT: "sort", _abi.GS_BINNING_GRID: "grid"}
 
 
 def default_cache() -> str:
     return os.environ.get("GS_TUNE_CACHE",
-                          os.path.join(os.path.expanduser("~"), ".cache", "gs_tune.json"))
+                          os.path.join(os.path.expanduser("~"), ".cache", "gs_tune.txt"))
 
 
-def signature(gs, views, with_grads: bool) -> str:
-    px = sum(v.out_h * v.out_w for v in views)
-    pairs = count_pairs(gs, views, tile=16)
-    dev = torch.cuda.get_device_name(gs[0].rho.device)
-    dt = str(gs[0].offset.dtype).replace("torch.", "")
-    return (f"{dev}|{dt}|{'fwdbwd' if with_grads else 'fwd'}|px{round(math.log2(max(px, 1)))}"
-            f"|img{round(math.log2(len(views)))}|ppp{round(math.log2(max(pairs, 1) / px * 256))}")
-
-
-def _time(plan: Plan, with_grads: bool, reps: int) -> float:
-    for _ in range(2):
-        plan.fwd()
-        if with_grads:
-            plan.bwd()
-    torch.cuda.synchronize()
-    ts = []
-    for _ in range(reps):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        plan.fwd()
-        if with_grads:
-            plan.bwd()
-        b.record()
-        b.synchronize()
-        ts.append(a.elapsed_time(b))
-    plan.status()
-    return sorted(ts)[len(ts) // 2]
-
-
-def tune(gs, views, with_grads: bool = True, candidates=CANDIDATES, reps: int = 5,
-         cache: str | None = None, refresh: bool = False) -> dict:
-    """-> {"tile": t, "batch": b, "ms": median ms, "table": {..}} for this
-    workload; reads and updates the JSON cache."""
+def tune(gs, views, with_grads: bool = True, reps: int = 5, cache: str | None = None,
+         stream=None) -> dict:
+    """-> {"tile", "batch", "binning", "adjoint", "ms", "from_cache", "n_timed"}
+    for this workload (the launch parameters to put in its views)."""
     cache = cache or default_cache()
-    key = signature(gs, views, with_grads)
-    with _lock:
-        table = {}
-        if os.path.exists(cache):
-            try:
-                with open(cache) as f:
-                    table = json.load(f)
-            except (OSError, ValueError):
-                table = {}
-        if key in table and not refresh:
-            return table[key]
-    results = {}
-    for tile, batch in candidates:
-        plan = Plan(gs, views, tile=tile, batch=batch, with_grads=with_grads)
-        if with_grads:
-            for go in plan.grad_outs:
-                go.normal_()
-        results[f"{tile}x{batch}"] = _time(plan, with_grads, reps)
-        del plan
-    best = min(results, key=results.get)
-    tile, batch = (int(x) for x in best.split("x"))
-    entry = {"tile": tile, "batch": batch, "ms": results[best], "table": results}
-    with _lock:
-        os.makedirs(os.path.dirname(cache) or ".", exist_ok=True)
-        table = {}
-        if os.path.exists(cache):
-            try:
-                with open(cache) as f:
-                    table = json.load(f)
-            except (OSError, ValueError):
-                table = {}
-        table[key] = entry
-        tmp = cache + f".{os.getpid()}.tmp"
-        with open(tmp, "w") as f:
-            json.dump(table, f, indent=1)
-        os.replace(tmp, cache)
-    return entry
+    os.makedirs(os.path.dirname(cache) or ".", exist_ok=True)
+    # tile 8 with the sorted pair list needs the most workspace: it fits every
+    # candidate
+    saved = [getattr(v, "binning", 0) for v in views]
+    for v in views:
+        v.binning = _abi.GS_BINNING_SORT
+    try:
+        plan = Plan(gs, views, tile=8, batch=32, with_grads=with_grads, stream=stream)
+    finally:
+        for v, b in zip(views, saved):
+            v.binning = b
+    if with_grads:
+        for go in plan.grad_outs:
+            go.normal_()
+    t = _abi.GsTuning()
+    lib = _abi.load()
+    st = lib.gs_tune(plan.n, plan.G, plan.V, plan.P_out, plan.P_go if with_grads else None,
+                     plan.P_gr if with_grads else None, plan.ws.ptr, plan.ws.nbytes,
+                     _stream(stream), int(reps), cache.encode(), ctypes.byref(t))
+    _abi.check(st, "gs_tune")
+    return {"tile": t.tile, "batch": t.batch, "binning": _BINNING.get(t.binning, t.binning),
+            "binning_code": t.binning, "adjoint": t.adjoint, "ms": float(t.ms),
+            "from_cache": bool(t.from_cache), "n_timed": t.n_timed}

@@ -1,7 +1,7 @@
-"""Autotuner: times the launch candidates on the workload, returns the
-fastest, and serves the cached choice on the next call."""
-import json
-
+"""Autotuner (gs_tune): times the launch candidates on the workload, returns
+the fastest, and serves the cached choice on the next call; the choice renders
+the same image."""
+import numpy as np
 import pytest
 
 import gs_synthetic as S
@@ -10,15 +10,36 @@ from _util import device_gaussians
 
 @pytest.mark.gpu
 def test_tune_picks_and_caches(tmp_path):
+    import torch
+    import paper_2501_06838_gb300 as gs
     from paper_2501_06838_gb300.tune import tune
     gsets, views = S.config3(n_images=4)
     dgs = [device_gaussians(g) for g in gsets]
-    cache = str(tmp_path / "tune.json")
-    cands = ((16, 32), (8, 32), (32, 64))
-    e1 = tune(dgs, views, with_grads=True, candidates=cands, reps=3, cache=cache)
-    assert (e1["tile"], e1["batch"]) in cands
-    assert e1["ms"] == min(e1["table"].values())
+    cache = str(tmp_path / "tune.txt")
+    e1 = tune(dgs, views, with_grads=True, reps=3, cache=cache)
+    assert e1["tile"] in (8, 16, 32) and e1["binning"] in ("sort", "grid")
+    assert not e1["from_cache"] and e1["n_timed"] == 12 and e1["ms"] > 0
     with open(cache) as f:
-        assert len(json.load(f)) == 1
-    e2 = tune(dgs, views, with_grads=True, candidates=cands, reps=3, cache=cache)
-    assert e2 == e1
+        assert len(f.read().splitlines()) == 1
+    e2 = tune(dgs, views, with_grads=True, reps=3, cache=cache)
+    assert e2["from_cache"] and (e2["tile"], e2["batch"], e2["binning"]) == \
+        (e1["tile"], e1["batch"], e1["binning"])
+    # the tuned launch renders the same image as the default one
+    for v in views:
+        v.binning = e1["binning_code"]
+    out_t, _ = gs.render_batched(dgs, views, tile=e1["tile"], batch=e1["batch"], check=True)
+    for v in views:
+        v.binning = 0
+    out_d, _ = gs.render_batched(dgs, views, check=True)
+    for a, b in zip(out_t, out_d):
+        assert torch.allclose(a, b, rtol=1e-5, atol=1e-6 * float(b.abs().max()))
+
+
+@pytest.mark.gpu
+def test_tune_rejects_bad_reps(tmp_path):
+    from paper_2501_06838_gb300 import _abi
+    from paper_2501_06838_gb300.tune import tune
+    gsets, views = S.config1()
+    with pytest.raises(_abi.GsError):
+        tune([device_gaussians(gsets[0])], views, with_grads=False, reps=0,
+             cache=str(tmp_path / "t.txt"))
