@@ -418,6 +418,15 @@ def run_gpu(args, rank, world, local_rank):
             tot = float(t.item())
         e2e["value"] = round(world * hr_pix * args.steps / (tot * 1e-3) / 1e6, 2)
         e2e["ms_per_step"] = round(tot / args.steps, 5)
+        pt = e2e.pop("pipelined_total_ms")
+        if world > 1:
+            t = torch.tensor([pt], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            pt = float(t.item())
+        e2e["pipelined"] = {"value": round(world * hr_pix * args.steps / (pt * 1e-3) / 1e6, 2),
+                            "ms_per_step": round(pt / args.steps, 5),
+                            "l2": "not flushed between the overlapping steps; every step copies "
+                                  "all its inputs in and all its results out"}
         res["e2e"] = e2e
 
     # ---- CPU baseline: the FP64 oracle on the host cores, bounded sample ----
@@ -489,55 +498,125 @@ def run_train(args, rank, world, local_rank):
             "final_loss": float(loss), "gpu_launches": int(launches), "clocks": clk}
 
 
-def run_e2e(args, plan, gsets, views, with_adj, dtname, dev, stream, flush):
-    """Same metric through Plan.fwd/bwd, with every step copying its inputs from
-    pinned host memory and its results back (copies inside the timed region)."""
+def _packed(specs, device):
+    """One pinned host buffer and one device buffer holding tensors of the given
+    (shape, dtype), each slice 256-byte aligned: a step's inputs (or results)
+    move in one copy."""
     import torch
-    host_in, dev_in = [], []
-    for g, dg in zip(gsets, plan.gs):
-        for t in dg.tensors():
-            h = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
-            h.copy_(t.cpu())
-            host_in.append(h)
-            dev_in.append(t)
-    if with_adj:
-        for go in plan.grad_outs:
-            h = torch.empty(go.shape, dtype=go.dtype, pin_memory=True)
-            h.copy_(go.cpu())
-            host_in.append(h)
-            dev_in.append(go)
-    host_out = [torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in plan.outs]
-    dev_out = list(plan.outs)
-    if with_adj:
-        host_out += [torch.empty(g.shape, dtype=g.dtype, pin_memory=True) for g in plan.grads]
-        dev_out += list(plan.grads)
-    h2d = sum(t.numel() * t.element_size() for t in host_in)
-    d2h = sum(t.numel() * t.element_size() for t in host_out)
+    offs, o = [], 0
+    for shape, dt in specs:
+        nb = math.prod(shape) * torch.empty((), dtype=dt).element_size()
+        offs.append((o, nb))
+        o = (o + nb + 255) // 256 * 256
+    host = torch.empty(max(o, 256), dtype=torch.uint8, pin_memory=True)
+    devb = torch.empty(max(o, 256), dtype=torch.uint8, device=device)
+    hv = [host[a:a + nb].view(dt).view(shape) for (a, nb), (shape, dt) in zip(offs, specs)]
+    dv = [devb[a:a + nb].view(dt).view(shape) for (a, nb), (shape, dt) in zip(offs, specs)]
+    return host, devb, hv, dv
 
-    def step():
-        for h, d in zip(host_in, dev_in):
-            d.copy_(h, non_blocking=True)
-        plan.fwd(stream)
+
+def _e2e_set(plan, with_adj, dev):
+    """A packed input/output buffer set and a Plan rendering from / into it."""
+    import torch
+    import importlib
+    R = importlib.import_module("paper_2501_06838_gb300.render")
+    in_specs = [(tuple(t.shape), t.dtype) for dg in plan.gs for t in dg.tensors()]
+    if with_adj:
+        in_specs += [(tuple(go.shape), go.dtype) for go in plan.grad_outs]
+    hin, din, hiv, div = _packed(in_specs, dev)
+    src = [t for dg in plan.gs for t in dg.tensors()] + (list(plan.grad_outs) if with_adj else [])
+    for h, t in zip(hiv, src):
+        h.copy_(t.cpu())
+    din.copy_(hin)   # the Plan sizes its workspace from the device parameters
+    out_specs = [(tuple(o.shape), o.dtype) for o in plan.outs]
+    if with_adj:
+        out_specs += [(tuple(g.shape), g.dtype) for g in plan.grads]
+    hout, dout, hov, dov = _packed(out_specs, dev)
+    gsd, k = [], 0
+    for dg in plan.gs:
+        gsd.append(R.Gaussians(*div[k:k + 5], ref_grid_m=dg.ref_grid_m, head=dg.head))
+        k += 5
+    nimg = len(plan.outs)
+    p = R.Plan(gsd, plan.views, tile=plan.V[0].tile, batch=plan.V[0].batch, with_grads=with_adj,
+               outs=dov[:nimg], grad_outs=div[k:] if with_adj else None,
+               grads=dov[nimg:] if with_adj else None)
+    return {"hin": hin, "din": din, "hout": hout, "dout": dout, "plan": p}
+
+
+def run_e2e(args, plan, gsets, views, with_adj, dtname, dev, stream, flush):
+    """Same metric through the public API with HOST buffers: every step copies
+    its inputs (parameters and upstream gradient, one packed pinned buffer) to
+    the device, renders (and runs the adjoint), and copies the image and the
+    gradients back (one packed buffer); copies inside the timed region.
+    value: serial steps (copy in, compute, copy out), L2 flushed before each.
+    pipelined: a stream of steps over two buffer sets, the copies of one step
+    overlapping the compute of its neighbours (copy-in, compute and copy-out
+    streams ordered by events; every step still moves all its bytes)."""
+    import torch
+    sets = [_e2e_set(plan, with_adj, dev) for _ in range(2)]
+    h2d = sets[0]["hin"].numel()
+    d2h = sets[0]["hout"].numel()
+
+    def serial(S):
+        S["din"].copy_(S["hin"], non_blocking=True)
+        S["plan"].fwd(stream)
         if with_adj:
-            plan.bwd(stream)
-        for d, h in zip(dev_out, host_out):
-            h.copy_(d, non_blocking=True)
+            S["plan"].bwd(stream)
+        S["hout"].copy_(S["dout"], non_blocking=True)
 
-    for _ in range(max(1, args.warmup)):
-        flush.zero_()
-        step()
+    with torch.cuda.stream(stream):
+        for _ in range(max(1, args.warmup)):
+            flush.zero_()
+            serial(sets[0])
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            serial(sets[0])
+            b.record(stream)
+            b.synchronize()
+            tot += a.elapsed_time(b)
+
+    s_in, s_cmp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    ev = {(k, i): torch.cuda.Event() for k in ("in", "cmp", "out") for i in (0, 1)}
+
+    def pipelined(steps):
+        for k in range(steps):
+            i = k & 1
+            S = sets[i]
+            if k >= 2:
+                s_in.wait_event(ev[("cmp", i)])      # inputs of step k - 2 consumed
+            with torch.cuda.stream(s_in):
+                S["din"].copy_(S["hin"], non_blocking=True)
+            ev[("in", i)].record(s_in)
+            s_cmp.wait_event(ev[("in", i)])
+            if k >= 2:
+                s_cmp.wait_event(ev[("out", i)])     # results of step k - 2 copied out
+            S["plan"].fwd(s_cmp)
+            if with_adj:
+                S["plan"].bwd(s_cmp)
+            ev[("cmp", i)].record(s_cmp)
+            s_out.wait_event(ev[("cmp", i)])
+            with torch.cuda.stream(s_out):
+                S["hout"].copy_(S["dout"], non_blocking=True)
+            ev[("out", i)].record(s_out)
+
+    pipelined(max(3, args.warmup))
     torch.cuda.synchronize()
-    tot = 0.0
-    for _ in range(args.steps):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        step()
-        b.record(stream)
-        b.synchronize()
-        tot += a.elapsed_time(b)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s_in)
+    pipelined(args.steps)
+    s_in.wait_stream(s_out)
+    b.record(s_in)
+    b.synchronize()
+    piped = a.elapsed_time(b)
+    for S in sets:
+        S["plan"].status()
     return {"unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-            "total_ms": tot}
+            "total_ms": tot, "pipelined_total_ms": piped,
+            "copies_per_step": {"h2d": 1, "d2h": 1}}
 
 
 def oracle_step(gsets, views, with_adj, band=None, threads=0, grad_outs=None):

@@ -298,18 +298,22 @@ class Plan:
     The calls are asynchronous and can be captured in a CUDA graph."""
 
     def __init__(self, gs, views, tile=0, batch=0, capacity=None, slack: float = 0.0,
-                 with_grads: bool = True, stream=None):
+                 with_grads: bool = True, stream=None, outs=None, grad_outs=None, grads=None):
+        """outs / grad_outs / grads: optional caller-allocated device tensors
+        ([3, out_h, out_w] float32 per image; [N_i, 9] float32 per image)."""
         self.gs, self.views = list(gs), list(views)
         self.n, self.G, self.V = _arrays(self.gs, self.views, tile, batch)
         dev = self.gs[0].rho.device
         self.ws = make_workspace(self.gs, self.views, capacity, tile, batch, slack, stream)
-        self.outs = [torch.empty((3, v.out_h, v.out_w), dtype=torch.float32, device=dev)
-                     for v in self.views]
+        self.outs = list(outs) if outs is not None else \
+            [torch.empty((3, v.out_h, v.out_w), dtype=torch.float32, device=dev) for v in self.views]
         self.P_out = (ctypes.c_void_p * self.n)(*[o.data_ptr() for o in self.outs])
         self.lib = _abi.load()
         if with_grads:
-            self.grad_outs = [torch.zeros_like(o) for o in self.outs]
-            self.grads = [torch.empty((g.n, 9), dtype=torch.float32, device=dev) for g in self.gs]
+            self.grad_outs = list(grad_outs) if grad_outs is not None else \
+                [torch.zeros_like(o) for o in self.outs]
+            self.grads = list(grads) if grads is not None else \
+                [torch.empty((g.n, 9), dtype=torch.float32, device=dev) for g in self.gs]
             self.P_go = (ctypes.c_void_p * self.n)(*[g.data_ptr() for g in self.grad_outs])
             self.P_gr = (ctypes.c_void_p * self.n)(*[g.data_ptr() for g in self.grads])
 
