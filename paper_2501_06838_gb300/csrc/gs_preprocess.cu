@@ -133,10 +133,12 @@ __device__ __forceinline__ int grid_root(int m) { return m == 1 ? 1 : m == 4 ? 2
 
 __global__ void __launch_bounds__(kFootprintBlock) k_preprocess(Ws w) {
   __shared__ unsigned long long sw[kFootprintBlock / 32 + 1];
-  // Clear the tile ranges (grid-stride) so empty tiles read (0, 0).
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < w.tiles;
-       t += (int64_t)gridDim.x * blockDim.x)
-    w.ranges[t] = make_uint2(0u, 0u);
+  // Sorted binning: clear the tile ranges (grid-stride) so empty tiles read
+  // (0, 0). Grid binning: the forward raster writes every tile's range.
+  if (!w.grid)
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < w.tiles;
+         t += (int64_t)gridDim.x * blockDim.x)
+      w.ranges[t] = make_uint2(0u, 0u);
 
   const int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   unsigned long long pix = 0ull;
@@ -270,15 +272,7 @@ __global__ void __launch_bounds__(kFootprintBlock) k_preprocess(Ws w) {
     trk = tr;
     if (!ok) atomicOr(&w.hdr->status, kStInvalid);
   }
-  // warp sum of the window areas, one atomic per warp
-  for (int o = 16; o > 0; o >>= 1) pix += __shfl_xor_sync(0xffffffffu, pix, o);
-  if ((threadIdx.x & 31) == 0 && pix) atomicAdd(&w.hdr->pixel_pairs, pix);
   if (w.grid) {
-    // pair count (no scan in grid mode) and the per-image reach: warp maxima
-    // when the whole warp is on one image, else one atomic per lane
-    unsigned long long c64 = cnt;
-    for (int o = 16; o > 0; o >>= 1) c64 += __shfl_xor_sync(0xffffffffu, c64, o);
-    if ((threadIdx.x & 31) == 0 && c64) atomicAdd(&w.hdr->pairs, c64);
     // pairs per tile, as per-row differences: +1 at the rectangle's first
     // tile of each of its rows, -1 just past its last (a tile's count is the
     // sum along its row up to it; the raster forms it). Lanes on the same entry in the same step add
@@ -299,25 +293,48 @@ __global__ void __launch_bounds__(kFootprintBlock) k_preprocess(Ws w) {
         if (endin && (__ffs(gb) - 1) == lane) atomicSub(w.tcount + b, (uint32_t)__popc(gb));
       }
     }
+    // the per-image reach: warp maxima when the whole warp is on one image,
+    // else per lane; an atomic only where the stored maximum is exceeded
+    // (every warp would otherwise queue on the same four words)
+    auto raise = [&](int im, int4 r) {
+      int* e = reinterpret_cast<int*>(w.ext + im);
+      const int4 cur = __ldcg(w.ext + im);
+      if (r.x > cur.x) atomicMax(e, r.x);
+      if (r.y > cur.y) atomicMax(e + 1, r.y);
+      if (r.z > cur.z) atomicMax(e + 2, r.z);
+      if (r.w > cur.w) atomicMax(e + 3, r.w);
+    };
     const int im0 = __shfl_sync(0xffffffffu, rim, 0);
     if (__all_sync(0xffffffffu, rim == im0 || rim < 0) && im0 >= 0) {
-      const int dl = __reduce_max_sync(0xffffffffu, reach.x);
-      const int dr = __reduce_max_sync(0xffffffffu, reach.y);
-      const int dt = __reduce_max_sync(0xffffffffu, reach.z);
-      const int db = __reduce_max_sync(0xffffffffu, reach.w);
-      if ((threadIdx.x & 31) == 0) {
-        int* e = reinterpret_cast<int*>(w.ext + im0);
-        atomicMax(e, dl); atomicMax(e + 1, dr); atomicMax(e + 2, dt); atomicMax(e + 3, db);
-      }
+      const int4 r = make_int4(__reduce_max_sync(0xffffffffu, reach.x),
+                               __reduce_max_sync(0xffffffffu, reach.y),
+                               __reduce_max_sync(0xffffffffu, reach.z),
+                               __reduce_max_sync(0xffffffffu, reach.w));
+      if ((threadIdx.x & 31) == 0) raise(im0, r);
     } else if (rim >= 0) {
-      int* e = reinterpret_cast<int*>(w.ext + rim);
-      atomicMax(e, reach.x); atomicMax(e + 1, reach.y); atomicMax(e + 2, reach.z); atomicMax(e + 3, reach.w);
+      raise(rim, reach);
     }
   }
-  // this block's pair count, scanned over blocks by k_scan_top
+  // this block's pair count, scanned over blocks by k_scan_top (sorted
+  // binning); grid binning adds the block total to P directly
   unsigned long long tot;
   block_exclusive_scan<unsigned long long, kFootprintBlock>(cnt, sw, tot);
-  if (threadIdx.x == 0 && blockIdx.x < w.scan_parts) w.parts[blockIdx.x] = tot;
+  if (threadIdx.x == 0) {
+    if (w.grid) {
+      if (tot) atomicAdd(&w.hdr->pairs, tot);
+    } else if (blockIdx.x < w.scan_parts) {
+      w.parts[blockIdx.x] = tot;
+    }
+  }
+  // block sum of the window areas, one atomic per block
+  for (int o = 16; o > 0; o >>= 1) pix += __shfl_xor_sync(0xffffffffu, pix, o);
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = pix;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long sp = 0ull;
+    for (int k = 0; k < kFootprintBlock / 32; ++k) sp += sw[k];
+    if (sp) atomicAdd(&w.hdr->pixel_pairs, sp);
+  }
 }
 
 // Chain rule from the record space to the parameters. The raster adjoint left,
