@@ -265,6 +265,16 @@ def ratio_ablation(scale: float = 4.0, r: float = 0.1, hr: int = 720):
                       window=WINDOW_RATIO)]
 
 
+def pipeline_input(scale: float, hr: int = 720, seed: int = 7) -> np.ndarray:
+    """LR image [3, lr, lr] float32 of the computational-cost table's shape
+    (a 720x720 crop down-scaled by s): the seeded image function sampled at
+    the LR pixel centres, lr = round(hr / s)."""
+    lr = int(round(hr / scale))
+    f = image_function(seed, lr)
+    ys, xs = np.mgrid[0:lr, 0:lr]
+    return f(xs, ys).astype(np.float32)
+
+
 def config5_scales(seed: int = 0, batch: int = 16):
     rng = np.random.Generator(np.random.PCG64(seed))
     return [float(np.float32(s)) for s in rng.uniform(1.0, 4.0, size=batch)]

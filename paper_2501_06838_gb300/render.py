@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import ctypes
 import dataclasses
+import math
 from typing import Sequence
 
 import torch
@@ -27,6 +28,33 @@ import torch
 from . import _abi
 
 _DTYPES = {torch.float32: _abi.GS_F32, torch.bfloat16: _abi.GS_BF16, torch.float16: _abi.GS_F16}
+
+WINDOW_SIGMA, WINDOW_RATIO = _abi.GS_WINDOW_SIGMA, _abi.GS_WINDOW_RATIO
+NORM_DENSITY, NORM_PEAK = _abi.GS_NORM_DENSITY, _abi.GS_NORM_PEAK
+ALIGN_EQ4, ALIGN_HALF = _abi.GS_ALIGN_EQ4, _abi.GS_ALIGN_HALF
+
+
+@dataclasses.dataclass
+class View:
+    """Output request (a gs_view): an out_h x out_w HR image of an lr_h x lr_w
+    LR grid at scale s (Eq. 4). window: WINDOW_SIGMA (|x/s - mu| <= k sigma,
+    k = trunc_k) or WINDOW_RATIO (Algorithm 1, ratio r = trunc_k); norm:
+    NORM_DENSITY (Eq. 2) or NORM_PEAK; align: ALIGN_EQ4 (x samples x / s) or
+    ALIGN_HALF ((x + 1/2) / s - 1/2)."""
+    lr_h: int
+    lr_w: int
+    out_h: int
+    out_w: int
+    scale: float
+    trunc_k: float = 3.0
+    norm: int = 0
+    window: int = 0
+    align: int = 0
+
+
+def out_size(lr: int, scale: float) -> int:
+    """floor(s * lr) with s rounded to float32 (the product is exact in double)."""
+    return int(math.floor(float(ctypes.c_float(scale).value) * lr))
 
 
 @dataclasses.dataclass

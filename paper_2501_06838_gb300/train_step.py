@@ -17,7 +17,7 @@ from __future__ import annotations
 import torch
 import torch.nn as nn
 
-from .render import GSRenderBatched
+from .render import GSRenderBatched, View, out_size
 
 
 class ResBlock(nn.Module):
@@ -77,7 +77,6 @@ class TrainStep:
         self.fused_head = fused_head
 
     def views(self, scales):
-        from gs_synthetic import View, out_size
         return [View(self.size, self.size, out_size(self.size, s), out_size(self.size, s), s,
                      norm=self.norm) for s in scales]
 
