@@ -174,6 +174,8 @@ __device__ __forceinline__ void gw_walk(const float* __restrict__ go, int64_t pl
 }
 
 __global__ void __launch_bounds__(kGwWarps * 32) k_raster_bwd_gw(Ws w) {
+  griddep_release();
+  griddep_wait();
   __shared__ float4 rt[kGwWarps][kGwRows];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int64_t gi = (int64_t)blockIdx.x * kGwWarps + wp;
@@ -204,8 +206,7 @@ cudaError_t launch_raster_bwd_gw(const Ws& w, cudaStream_t s) {
   if (w.n == 0) return cudaSuccess;
   LaunchScope ls(kKRasterBwdGw, s);
   const int64_t blocks = (w.n + kGwWarps - 1) / kGwWarps;
-  k_raster_bwd_gw<<<(unsigned)blocks, kGwWarps * 32, 0, s>>>(w);
-  return cudaGetLastError();
+  return launch_chain(k_raster_bwd_gw, dim3((unsigned)blocks), dim3(kGwWarps * 32), 0, s, w);
 }
 
 }  // namespace gs

@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -392,12 +393,9 @@ gs_status run_backward(int32_t n_images, const gs_gaussians* g, const gs_view* v
   if (c.w.n == 0) return GS_OK;
   cudaError_t e;
   if (c.P.adjoint == GS_ADJOINT_TILE) {
-    {
-      // the tile adjoint adds into the record-space accumulators
-      LaunchScope ls(kKMemset, s);
-      e = cudaMemsetAsync(c.w.grec, 0, 48 * (size_t)c.w.n, s);
-      if (e != cudaSuccess) return cuda_fail(e, "memset");
-    }
+    // the tile adjoint adds into the record-space accumulators
+    e = launch_zero(c.w.grec, 48 * (size_t)c.w.n, s);
+    if (e != cudaSuccess) return cuda_fail(e, "memset");
     const int fb = c.passes & 1;
     e = launch_raster_bwd(c.w, c.w.grid ? c.w.vals[0] : c.w.vals[fb], c.P.batch, s);
     if (e != cudaSuccess) return cuda_fail(e, "raster_bwd");
@@ -432,6 +430,11 @@ const char* status_text(uint32_t bits) {
 namespace gs {
 
 void set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
+bool chain_overlap() {
+  static const bool on = std::getenv("GS_NO_PDL") == nullptr;
+  return on;
+}
 
 void launch_begin(int id, cudaStream_t s) {
   g_launches.fetch_add(1, std::memory_order_relaxed);

@@ -28,6 +28,8 @@ constexpr int kSortBlock = kSortThreads * kSortItems;    // 2048 pairs per block
 // total is the pair count P: it is stored and checked against the capacity.
 __global__ void __launch_bounds__(kTopThreads) k_scan_top(unsigned long long* parts, int nparts,
                                                           Header* hdr, int count_mode) {
+  griddep_release();
+  griddep_wait();
   __shared__ unsigned long long sw[kTopThreads / 32 + 1];
   unsigned long long carry = 0ull;
   for (int c = 0; c < nparts; c += kTopThreads) {
@@ -49,6 +51,8 @@ __global__ void __launch_bounds__(kTopThreads) k_scan_top(unsigned long long* pa
 // the counts. One lane per Gaussian gathers its tile rectangle; the warp then
 // writes each of its 32 Gaussians' pairs cooperatively (coalesced stores).
 __global__ void __launch_bounds__(kFootprintBlock) k_emit(Ws w) {
+  griddep_release();
+  griddep_wait();
   __shared__ unsigned long long sw[kFootprintBlock / 32 + 1];
   const unsigned long long P = effective_pairs(w.hdr);
   if (P == 0ull) return;   // uniform over the grid
@@ -83,6 +87,8 @@ __global__ void __launch_bounds__(kFootprintBlock) k_emit(Ws w) {
 template <int BITS>
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* keys, const Header* hdr,
                                                              int shift, uint32_t* hist, int nblk) {
+  griddep_release();
+  griddep_wait();
   constexpr int R = 1 << BITS;
   __shared__ uint32_t h[kSortWarps][R];
   for (int i = threadIdx.x; i < kSortWarps * R; i += kSortThreads) (&h[0][0])[i] = 0u;
@@ -111,6 +117,8 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* key
 // hist[d][0..nblk) and writes the row total to dtot[d].
 __global__ void __launch_bounds__(kSortThreads) k_radix_rowscan(uint32_t* hist, int nblk,
                                                                 uint32_t* dtot) {
+  griddep_release();
+  griddep_wait();
   __shared__ unsigned long long sw[kSortThreads / 32 + 1];
   uint32_t* row = hist + (int64_t)blockIdx.x * nblk;
   unsigned long long carry = 0ull;
@@ -140,6 +148,8 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
                                                                 uint32_t* vout, const Header* hdr,
                                                                 int shift, const uint32_t* hist,
                                                                 const uint32_t* dtot, int nblk) {
+  griddep_release();
+  griddep_wait();
   constexpr int R = 1 << BITS;
   constexpr int DPT = R / kSortThreads;   // digits per thread in the digit scans
   extern __shared__ uint32_t sm[];
@@ -250,6 +260,7 @@ size_t scatter_smem() {
 
 __global__ void __launch_bounds__(256) k_ranges(const uint32_t* keys, const Header* hdr,
                                                 uint2* ranges) {
+  griddep_wait();
   const unsigned long long P = effective_pairs(hdr);
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if ((unsigned long long)i >= P) return;
@@ -267,32 +278,32 @@ int sort_blocks_needed(int64_t capacity) { return (int)((capacity + kSortBlock -
 cudaError_t launch_scan_counts(const Ws& w, cudaStream_t s) {
   const int parts = scan_parts_needed(w.n);
   LaunchScope ls(kKScanTop, s);
-  k_scan_top<<<1, kTopThreads, 0, s>>>(w.parts, parts, w.hdr, 1);
-  return cudaGetLastError();
+  return launch_chain(k_scan_top, dim3(1), dim3(kTopThreads), 0, s, w.parts, parts, w.hdr, 1);
 }
 
 cudaError_t launch_emit(const Ws& w, cudaStream_t s) {
   if (w.n == 0) return cudaSuccess;
   const int blocks = scan_parts_needed(w.n);
   LaunchScope ls(kKEmit, s);
-  k_emit<<<blocks, kFootprintBlock, 0, s>>>(w);
-  return cudaGetLastError();
+  return launch_chain(k_emit, dim3(blocks), dim3(kFootprintBlock), 0, s, w);
 }
 
 template <int BITS>
 cudaError_t sort_pass(const Ws& w, int shift, int cur, cudaStream_t s) {
+  cudaError_t e0;
   {
     LaunchScope ls(kKRadixHist, s);
-    k_radix_hist<BITS><<<w.sort_blocks, kSortThreads, 0, s>>>(w.keys[cur], w.hdr, shift, w.hist,
-                                                              w.sort_blocks);
+    e0 = launch_chain(k_radix_hist<BITS>, dim3(w.sort_blocks), dim3(kSortThreads), 0, s,
+                      (const uint32_t*)w.keys[cur], (const Header*)w.hdr, shift, w.hist,
+                      w.sort_blocks);
   }
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = e0;
   if (e != cudaSuccess) return e;
   {
     LaunchScope ls(kKRadixRowscan, s);
-    k_radix_rowscan<<<1 << BITS, kSortThreads, 0, s>>>(w.hist, w.sort_blocks, w.hscan);
+    e = launch_chain(k_radix_rowscan, dim3(1 << BITS), dim3(kSortThreads), 0, s, w.hist,
+                     w.sort_blocks, w.hscan);
   }
-  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t smem = scatter_smem<BITS>();
   static bool smem_set = false;   // opt in to > 48 KB once per process
@@ -304,11 +315,12 @@ cudaError_t sort_pass(const Ws& w, int shift, int cur, cudaStream_t s) {
   }
   {
     LaunchScope ls(kKRadixScatter, s);
-    k_radix_scatter<BITS><<<w.sort_blocks, kSortThreads, smem, s>>>(
-        w.keys[cur], w.vals[cur], w.keys[cur ^ 1], w.vals[cur ^ 1], w.hdr, shift, w.hist, w.hscan,
-        w.sort_blocks);
+    e = launch_chain(k_radix_scatter<BITS>, dim3(w.sort_blocks), dim3(kSortThreads), smem, s,
+                     (const uint32_t*)w.keys[cur], (const uint32_t*)w.vals[cur], w.keys[cur ^ 1],
+                     w.vals[cur ^ 1], (const Header*)w.hdr, shift, (const uint32_t*)w.hist,
+                     (const uint32_t*)w.hscan, w.sort_blocks);
   }
-  return cudaGetLastError();
+  return e;
 }
 
 // Stable LSD sort of the tile keys: `bits` significant bits in passes of at
@@ -333,8 +345,8 @@ cudaError_t launch_ranges(const Ws& w, const uint32_t* sorted_keys, cudaStream_t
   if (w.capacity == 0) return cudaSuccess;
   const int blocks = (int)((w.capacity + 255) / 256);
   LaunchScope ls(kKRanges, s);
-  k_ranges<<<blocks, 256, 0, s>>>(sorted_keys, w.hdr, w.ranges);
-  return cudaGetLastError();
+  return launch_chain(k_ranges, dim3(blocks), dim3(256), 0, s, sorted_keys, (const Header*)w.hdr,
+                      w.ranges);
 }
 
 }  // namespace gs

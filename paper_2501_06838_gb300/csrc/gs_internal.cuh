@@ -215,6 +215,7 @@ __device__ __forceinline__ unsigned long long effective_pairs(const Header* h) {
 cudaError_t launch_setup(const SetupChunk& c, const Ws& w, cudaStream_t s);
 cudaError_t launch_preprocess(const Ws& w, cudaStream_t s);
 cudaError_t launch_preprocess_bwd(const Ws& w, cudaStream_t s);
+cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t s);   // bytes: a multiple of 16
 cudaError_t launch_scan_counts(const Ws& w, cudaStream_t s);
 cudaError_t launch_emit(const Ws& w, cudaStream_t s);
 cudaError_t launch_sort(const Ws& w, int key_bits, cudaStream_t s, int* final_buf);
@@ -234,6 +235,40 @@ enum KernelId {
 // begin/end so that the launch counter and the optional event timing see it.
 void launch_begin(int kernel_id, cudaStream_t s);
 void launch_end(int kernel_id, cudaStream_t s);
+
+// Programmatic dependent launch. Every kernel of the render's launch chains
+// starts with griddep_wait(): it waits until the kernel before it in the
+// stream has completed and its memory is visible (the waiting is the
+// hardware's; a kernel launched without the attribute passes straight
+// through). A kernel whose successor is a short pass also starts with
+// griddep_release(), which lets that successor be scheduled while this one
+// drains; kernels followed by a raster pass leave the release to their exit,
+// so that the raster's single wave of CTAs is spread over the SMs as usual.
+__device__ __forceinline__ void griddep_wait() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+}
+__device__ __forceinline__ void griddep_release() {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+bool chain_overlap();   // false when the environment sets GS_NO_PDL (launch-mode comparisons)
+
+// Launch one kernel of a chain with programmatic stream serialization.
+template <typename... P, typename... A>
+cudaError_t launch_chain(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                         A... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = chain_overlap() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<P>(args)...);
+}
 
 struct LaunchScope {
   int id;

@@ -17,6 +17,8 @@ constexpr float kLn2 = 0.6931471805599453f;
 constexpr float kLog2TwoPi = 2.6514961294723187f;
 
 __global__ void k_setup(SetupChunk c, Ws w) {
+  griddep_release();
+  griddep_wait();
   const int t = threadIdx.x;
   if (c.reset && w.grid)   // clear the per-tile pair counts of grid binning
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + t; i < w.tiles; i += (int64_t)gridDim.x * blockDim.x)
@@ -132,6 +134,7 @@ __device__ __forceinline__ void head_jacobian(const ImageDesc& D, const float (&
 __device__ __forceinline__ int grid_root(int m) { return m == 1 ? 1 : m == 4 ? 2 : m == 9 ? 3 : 4; }
 
 __global__ void __launch_bounds__(kFootprintBlock) k_preprocess(Ws w) {
+  griddep_wait();
   __shared__ unsigned long long sw[kFootprintBlock / 32 + 1];
   // Sorted binning: clear the tile ranges (grid-stride) so empty tiles read
   // (0, 0). Grid binning: the forward raster writes every tile's range.
@@ -350,6 +353,8 @@ __global__ void __launch_bounds__(kFootprintBlock) k_preprocess(Ws w) {
 // C = -L2/(2 s^2 sy^2 D), l = -log2(2 pi sx sy sqrt D) (density) or 0 (peak),
 // colour record = alpha c (L2 = log2 e, so ln2 * L2 = 1).
 __global__ void __launch_bounds__(256) k_preprocess_bwd(Ws w) {
+  griddep_release();
+  griddep_wait();
   const int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (gi >= w.n) return;
   const int im = image_of_gaussian(w.images, w.n_images, gi);
@@ -407,8 +412,7 @@ cudaError_t launch_setup(const SetupChunk& c, const Ws& w, cudaStream_t s) {
   LaunchScope ls(kKSetup, s);
   int blocks = 1;
   if (c.reset && w.grid) blocks = (int)std::min<int64_t>(1024, std::max<int64_t>(1, ((int64_t)w.tiles + 255) / 256));
-  k_setup<<<blocks, 256, 0, s>>>(c, w);
-  return cudaGetLastError();
+  return launch_chain(k_setup, dim3(blocks), dim3(256), 0, s, c, w);
 }
 
 cudaError_t launch_preprocess(const Ws& w, cudaStream_t s) {
@@ -416,16 +420,33 @@ cudaError_t launch_preprocess(const Ws& w, cudaStream_t s) {
   int blocks = (int)((work + kFootprintBlock - 1) / kFootprintBlock);
   if (blocks < 1) blocks = 1;
   LaunchScope ls(kKPreprocess, s);
-  k_preprocess<<<blocks, kFootprintBlock, 0, s>>>(w);
-  return cudaGetLastError();
+  return launch_chain(k_preprocess, dim3(blocks), dim3(kFootprintBlock), 0, s, w);
 }
 
 cudaError_t launch_preprocess_bwd(const Ws& w, cudaStream_t s) {
   if (w.n == 0) return cudaSuccess;
   int blocks = (int)((w.n + 255) / 256);
   LaunchScope ls(kKPreprocessBwd, s);
-  k_preprocess_bwd<<<blocks, 256, 0, s>>>(w);
-  return cudaGetLastError();
+  return launch_chain(k_preprocess_bwd, dim3(blocks), dim3(256), 0, s, w);
+}
+
+namespace {
+__global__ void __launch_bounds__(256) k_zero(float4* p, int64_t n4) {
+  griddep_wait();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+}  // namespace
+
+// Zero a 16-byte-aligned buffer in the chain (a kernel, so that the launches
+// around it overlap as the rest of the chain does).
+cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t s) {
+  const int64_t n4 = (int64_t)(bytes / 16);
+  if (n4 == 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>(4 * 152, (n4 + 255) / 256);
+  LaunchScope ls(kKMemset, s);
+  return launch_chain(k_zero, dim3(blocks), dim3(256), 0, s, reinterpret_cast<float4*>(p), n4);
 }
 
 }  // namespace gs

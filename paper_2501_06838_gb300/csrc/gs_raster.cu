@@ -273,6 +273,8 @@ __device__ __forceinline__ void fwd_gaussian(float2 (&acc)[NQ][3], const FwdOps<
 
 template <int TILE, int BY, int PF, bool GRID>
 __global__ void __launch_bounds__(TILE * TILE / BY) k_raster_fwd(Ws w, const uint32_t* vals) {
+  griddep_release();
+  griddep_wait();
   constexpr int NT = TILE * TILE / BY, BATCH = NT * PF, NQ = BY / 2, HP = TILE / 2;
   __shared__ __align__(16) float4 raw[2][BATCH * kRecordF4];
   __shared__ float4 gA[BATCH], gB[BATCH], gC[BATCH];
@@ -472,6 +474,8 @@ __device__ __forceinline__ void bwd_gaussian(const float2 (&g)[NQ][3], const Bwd
 
 template <int TILE, int BY, int PF>
 __global__ void __launch_bounds__(TILE * TILE / BY) k_raster_bwd(Ws w, const uint32_t* vals) {
+  griddep_release();
+  griddep_wait();
   constexpr int NT = TILE * TILE / BY, NW = NT / 32, BATCH = NT * PF, NQ = BY / 2, HP = TILE / 2;
   __shared__ __align__(16) float4 raw[2][BATCH * kRecordF4];
   __shared__ float4 gA[BATCH], gB[BATCH], gC[BATCH], gD[BATCH];
@@ -593,13 +597,11 @@ cudaError_t run(const Ws& w, const uint32_t* vals, bool bwd, cudaStream_t s) {
   constexpr int NT = TILE * TILE / BY;
   if (bwd) {
     LaunchScope ls(kKRasterBwd, s);
-    k_raster_bwd<TILE, BY, PF><<<w.tiles, NT, 0, s>>>(w, vals);
-  } else {
-    LaunchScope ls(kKRasterFwd, s);
-    if (w.grid) k_raster_fwd<TILE, BY, PF, true><<<w.tiles, NT, 0, s>>>(w, vals);
-    else k_raster_fwd<TILE, BY, PF, false><<<w.tiles, NT, 0, s>>>(w, vals);
+    return launch_chain(k_raster_bwd<TILE, BY, PF>, dim3(w.tiles), dim3(NT), 0, s, w, vals);
   }
-  return cudaGetLastError();
+  LaunchScope ls(kKRasterFwd, s);
+  if (w.grid) return launch_chain(k_raster_fwd<TILE, BY, PF, true>, dim3(w.tiles), dim3(NT), 0, s, w, vals);
+  return launch_chain(k_raster_fwd<TILE, BY, PF, false>, dim3(w.tiles), dim3(NT), 0, s, w, vals);
 }
 
 // Launch configurations: tile edge -> rows per thread (threads = TILE^2 / BY);
