@@ -254,6 +254,36 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # The GPU arm
 # --------------------------------------------------------------------------
+# Algorithmic DRAM bytes of the memory-bound passes (per launch): the footprint
+# pass reads each Gaussian's parameters and writes its 64-byte record (and, with
+# grid binning, its 8-byte compact window); the chain rule reads parameters and
+# the 48 bytes of record-space moments and writes 36 bytes of gradients; the
+# clearing writes the moments; with sorted binning the emit pass writes 8 bytes
+# per (tile, Gaussian) pair (reading 16 bytes of each record), a radix histogram
+# pass reads the 4-byte keys, a scatter pass reads and writes keys and values
+# (16 bytes per pair) and the ranges pass reads the keys.
+def hbm_stage_rates(stage_raw, steps, stats, dtname, grid):
+    n, pairs = stats["n_gaussians"], stats["tile_pairs"]
+    pb = {"f32": 36, "bf16": 18, "f16": 18}[dtname]
+    per_launch = {"preprocess": n * (pb + 64 + (8 if grid else 0)),
+                  "preprocess_bwd": n * (pb + 48 + 36), "memset": n * 48,
+                  "emit": pairs * 8 + n * 16, "radix_hist": pairs * 4,
+                  "radix_scatter": pairs * 16, "ranges": pairs * 4}
+    peak = float(load_peaks()[0].get("hbm_gbs", 6800.0))
+    out = {}
+    for k, b in per_launch.items():
+        if k not in stage_raw or b == 0:
+            continue
+        ms, cnt = stage_raw[k]
+        if cnt == 0 or ms <= 0:
+            continue
+        gbs = b * cnt / (ms * 1e-3) / 1e9
+        out[k] = {"bytes_per_launch": int(b), "launches_per_step": cnt // steps,
+                  "ms_per_launch": round(ms / cnt, 5), "achieved_gbs": round(gbs, 1),
+                  "frac_of_measured_hbm": round(gbs / peak, 4)}
+    return out
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -368,7 +398,10 @@ def run_gpu(args, rank, world, local_rank):
         step()
     torch.cuda.synchronize()
     gs.timing_enable([])
-    stage = {k: round(v[0] / 3, 5) for k, v in gs.timing_read().items()}
+    stage_raw = gs.timing_read()
+    stage = {k: round(v[0] / 3, 5) for k, v in stage_raw.items()}
+    hbm_stages = hbm_stage_rates(stage_raw, 3, stats, dtname,
+                                 binning_desc(plan.V[0].binning, gsets, views) == "grid-implicit")
 
     # ---- measured unit throughputs (the ALU roofline's inputs) ----
     unit_rates = None
@@ -430,6 +463,7 @@ def run_gpu(args, rank, world, local_rank):
                           "adjoint) in a second pass of the same steps",
         "stage_ms_per_step": stage,
         "pairs": {"pixel_pairs": stats["pixel_pairs"], "tile_pairs": stats["tile_pairs"]},
+        "hbm_stages": hbm_stages,
         "roofline": roof, "gpu_launches": int(launches), "clocks": clk,
         "unit_rates": unit_rates,
     }
