@@ -131,11 +131,14 @@ __device__ __forceinline__ void head_jacobian(const ImageDesc& D, const float (&
   J[8] = p.al * (1.0f - p.al);
 }
 
+constexpr int kCountBand = 512;   // entries of a warp's tile-count table (grid binning)
+
 __device__ __forceinline__ int grid_root(int m) { return m == 1 ? 1 : m == 4 ? 2 : m == 9 ? 3 : 4; }
 
 __global__ void __launch_bounds__(kFootprintBlock) k_preprocess(Ws w) {
   griddep_wait();
   __shared__ unsigned long long sw[kFootprintBlock / 32 + 1];
+  __shared__ int band[kFootprintBlock / 32][kCountBand];   // grid binning: per-warp count table
   // Sorted binning: clear the tile ranges (grid-stride) so empty tiles read
   // (0, 0). Grid binning: the forward raster writes every tile's range.
   if (!w.grid)
@@ -150,6 +153,7 @@ __global__ void __launch_bounds__(kFootprintBlock) k_preprocess(Ws w) {
   int rim = -1;                          // image of `reach` (-1: none)
   uint4 trk = make_uint4(0u, 0u, 0u, 0u);  // tile rectangle, for the per-tile counts
   uint32_t tcol0 = 0u;                     // its first tile column in the image
+  int tim = -1, tty0 = 0, tty1 = -1;       // its image and tile rows
   if (gi < w.n) {
     const int im = image_of_gaussian(w.images, w.n_images, gi);
     const ImageDesc& D = w.images[im];
@@ -268,6 +272,9 @@ __global__ void __launch_bounds__(kFootprintBlock) k_preprocess(Ws w) {
       cnt = tw * th;
       tr = make_uint4((uint32_t)(D.t_base + ty0 * D.tiles_x + tx0), (uint32_t)D.tiles_x, tw, th);
       tcol0 = (uint32_t)tx0;
+      tim = im;
+      tty0 = ty0;
+      tty1 = ty1;
       pix = (unsigned long long)(x1 - x0 + 1) * (unsigned long long)(y1 - y0 + 1);
     }
     w.trect[gi] = tr;
@@ -278,19 +285,57 @@ __global__ void __launch_bounds__(kFootprintBlock) k_preprocess(Ws w) {
   if (w.grid) {
     // pairs per tile, as per-row differences: +1 at the rectangle's first
     // tile of each of its rows, -1 just past its last (a tile's count is the
-    // sum along its row up to it; the raster forms it). Lanes on the same entry in the same step add
-    // together: one atomic per entry and step.
-    {
-      const int lane = threadIdx.x & 31;
+    // sum along its row up to it; the raster forms it).
+    const int lane = threadIdx.x & 31;
+    const bool act = cnt != 0u;
+    const unsigned am = __ballot_sync(0xffffffffu, act);
+    const int lead = am ? __ffs(am) - 1 : 0;
+    const int imL = __shfl_sync(0xffffffffu, tim, lead);
+    const bool same = __all_sync(0xffffffffu, !act || tim == imL);
+    // The warp's tile band (rows RY0..RY1, columns CX0..CX1, the -1 entries
+    // included): when the whole warp is on one image and the band fits, the
+    // differences are first summed in a per-warp shared-memory table and each
+    // nonzero entry is added once; otherwise lanes on the same entry combine
+    // by warp match.
+    const int tilesx = (int)__shfl_sync(0xffffffffu, trk.y, lead);
+    const int lastc = act ? (int)(tcol0 + trk.z) : 0;        // column just past the rectangle
+    const int RY0 = __reduce_min_sync(0xffffffffu, act ? tty0 : 0x7fffffff);
+    const int RY1 = __reduce_max_sync(0xffffffffu, act ? tty1 : -1);
+    const int CX0 = __reduce_min_sync(0xffffffffu, act ? (int)tcol0 : 0x7fffffff);
+    const int CX1 = __reduce_max_sync(0xffffffffu, act ? min(lastc, tilesx - 1) : -1);
+    const int bw = CX1 - CX0 + 1, bh = RY1 - RY0 + 1;
+    if (am != 0u && same && bw > 0 && bh > 0 && bw * bh <= kCountBand) {
+      int* h = band[threadIdx.x >> 5];
+      const int span = bw * bh;
+      for (int e = lane; e < span; e += 32) h[e] = 0;
+      __syncwarp();
+      if (act) {
+        const int c0 = (int)tcol0 - CX0, c1 = lastc - CX0;
+        const bool endin = lastc < tilesx;
+        for (int r = tty0 - RY0; r <= tty1 - RY0; ++r) {
+          atomicAdd(h + r * bw + c0, 1);
+          if (endin) atomicSub(h + r * bw + c1, 1);
+        }
+      }
+      __syncwarp();
+      const int64_t base = w.images[imL].t_base + (int64_t)RY0 * tilesx + CX0;
+      for (int e = lane; e < span; e += 32) {
+        const int v = h[e];
+        if (v != 0) {
+          const int rr = e / bw;
+          atomicAdd(w.tcount + base + (int64_t)rr * tilesx + (e - rr * bw), (uint32_t)v);
+        }
+      }
+    } else if (am != 0u) {
       const uint32_t rows = cnt ? trk.w : 0u;
       const uint32_t last = tcol0 + trk.z;   // column just past the rectangle
       for (uint32_t k = 0;; ++k) {
-        const bool act = k < rows;
-        if (!__any_sync(0xffffffffu, act)) break;
-        const uint32_t a = act ? trk.x + k * trk.y : 0xffffffffu;
+        const bool on = k < rows;
+        if (!__any_sync(0xffffffffu, on)) break;
+        const uint32_t a = on ? trk.x + k * trk.y : 0xffffffffu;
         const unsigned ga = __match_any_sync(0xffffffffu, a);
-        if (act && (__ffs(ga) - 1) == lane) atomicAdd(w.tcount + a, (uint32_t)__popc(ga));
-        const bool endin = act && last < trk.y;
+        if (on && (__ffs(ga) - 1) == lane) atomicAdd(w.tcount + a, (uint32_t)__popc(ga));
+        const bool endin = on && last < trk.y;
         const uint32_t b = endin ? a + trk.z : 0xffffffffu;
         const unsigned gb = __match_any_sync(0xffffffffu, b);
         if (endin && (__ffs(gb) - 1) == lane) atomicSub(w.tcount + b, (uint32_t)__popc(gb));
