@@ -168,7 +168,13 @@ typedef struct gs_view {
   int32_t align;        /* gs_align */
   int32_t adjoint;      /* gs_adjoint; every view of one batched call must agree */
   int32_t binning;      /* gs_binning; every view of one batched call must agree */
-  int32_t reserved;     /* must be 0 */
+  int32_t row0;         /* first image row this view renders (0: the whole image). The output
+                           holds rows row0 .. row0 + out_h - 1 of the image: a horizontal band,
+                           with row0 + out_h <= floor(s * lr_h) + 1. Windows and exponents are
+                           those of the whole image, so the bands of a partition render the same
+                           pixels bit for bit and their adjoints sum to the whole image's (the
+                           row split of one image over several devices, one sum of the
+                           gradients). */
 } gs_view;
 
 /* Counters of the last forward call on a workspace. */

@@ -50,7 +50,7 @@ class GsView(ctypes.Structure):
                 ("norm", ctypes.c_int32), ("tile", ctypes.c_int32),
                 ("batch", ctypes.c_int32), ("window", ctypes.c_int32),
                 ("align", ctypes.c_int32), ("adjoint", ctypes.c_int32),
-                ("binning", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("binning", ctypes.c_int32), ("row0", ctypes.c_int32)]
 
 
 class GsStats(ctypes.Structure):

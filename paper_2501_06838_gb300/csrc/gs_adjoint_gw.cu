@@ -187,9 +187,10 @@ __global__ void __launch_bounds__(kGwWarps * 32) k_raster_bwd_gw(Ws w) {
   float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   if (x0 <= x1 && y0 <= y1) {   // warp-uniform
     const ImageDesc& D = w.images[image_of_gaussian(w.images, w.n_images, gi)];
-    const float* go = w.direct ? w.grad_out0 : D.grad_out;
     const int W = D.out_w;
     const int64_t plane = (int64_t)D.out_h * W;
+    // rows are image rows; the upstream gradient holds rows row0 .. row0 + out_h - 1
+    const float* go = (w.direct ? w.grad_out0 : D.grad_out) - (int64_t)D.row0 * W;
     const bool aligned = (W & 1) == 0 && (reinterpret_cast<uintptr_t>(go) & 7) == 0;
     if (aligned)
       gw_walk<true>(go, plane, W, x0, x1, y0, y1, rec[0], rec[1], rec[2], rt[wp], lane, v);

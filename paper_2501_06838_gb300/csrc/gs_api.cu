@@ -159,13 +159,13 @@ gs_status validate(int32_t n_images, const gs_gaussians* g, const gs_view* v, Pr
     if (V.adjoint != v[0].adjoint)
       return fail(GS_ERR_INVALID, "image %lld: adjoint differs from image 0", (long long)i);
     if (V.binning < 0 || V.binning > 2) return fail(GS_ERR_INVALID, "image %lld: unknown binning", (long long)i);
-    if (V.reserved != 0) return fail(GS_ERR_INVALID, "image %lld: reserved must be 0", (long long)i);
+    if (V.row0 < 0) return fail(GS_ERR_INVALID, "image %lld: row0 < 0", (long long)i);
     if (V.binning != v[0].binning)
       return fail(GS_ERR_INVALID, "image %lld: binning differs from image 0", (long long)i);
     if (G.ref_grid_m == 0 || V.out_w > 32767 || V.out_h > 32767) grid_ok = false;
     const double sh = std::floor((double)V.scale * V.lr_h) + 1.0;
     const double sw = std::floor((double)V.scale * V.lr_w) + 1.0;
-    if ((double)V.out_h > sh || (double)V.out_w > sw)
+    if ((double)V.out_h + (double)V.row0 > sh || (double)V.out_w > sw)
       return fail(GS_ERR_INVALID, "image %lld: output larger than floor(s * lr) + 1", (long long)i);
     if (tile_of(V) != P->tile || batch_of(V) != P->batch)
       return fail(GS_ERR_INVALID, "image %lld: tile/batch differ from image 0", (long long)i);
@@ -305,6 +305,7 @@ gs_status upload_images(const Call& c, const gs_gaussians* g, const gs_view* v, 
       d.lr_w = v[i].lr_w;
       d.out_h = v[i].out_h;
       d.out_w = v[i].out_w;
+      d.row0 = v[i].row0;
       d.scale = v[i].scale;
       d.trunc_k = v[i].trunc_k;
       d.flags = (v[i].norm == GS_NORM_PEAK ? kFlagPeak : 0) |

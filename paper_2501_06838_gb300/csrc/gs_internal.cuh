@@ -35,7 +35,8 @@ struct ImageDesc {
   // rho = h_rho_scale tanh(raw), c = alpha = sigmoid(raw),
   // o = h_offset_scale raw (or tanh(raw) with kFlagOffsetTanh)
   float h_sigma_lo, h_sigma_span, h_rho_scale, h_offset_scale;
-  int32_t pad_[4];
+  int32_t row0;   // first image row of the output (a band; 0: the whole image)
+  int32_t pad_[3];
 };
 // ImageDesc::flags
 constexpr int32_t kFlagPeak = 1;   // Z = 1 instead of Eq. 2's normalisation

@@ -46,18 +46,19 @@ __global__ void k_setup(SetupChunk c, Ws w) {
 //     r = (s * k) * sigma, lo = ceil(c - r), hi = floor(c + r);
 //   ratio box (Algorithm 1's rasterization ratio, extent L = lr_w or lr_h), open:
 //     r = (s * k) * L, lo = floor(c - r) + 1, hi = ceil(c + r) - 1;
-// lo clamped to >= 0, hi to <= n_out - 1; empty -> lo = 1, hi = 0.
+// lo clamped to >= first, hi to <= last (the rendered rows or columns);
+// empty -> lo = 1, hi = 0 (relative to first).
 __device__ __forceinline__ void window_axis(float c, float sig, int lr_extent, float s, float k,
-                                            bool ratio, int n_out, int& lo, int& hi) {
+                                            bool ratio, int first, int last_i, int& lo, int& hi) {
   float sk = __fmul_rn(s, k);
   float r = __fmul_rn(sk, ratio ? (float)lr_extent : sig);
   float a = __fsub_rn(c, r), b = __fadd_rn(c, r);
   float flo = ratio ? __fadd_rn(floorf(a), 1.0f) : ceilf(a);
   float fhi = ratio ? __fsub_rn(ceilf(b), 1.0f) : floorf(b);
-  float last = (float)(n_out - 1);
-  if (!(flo >= 0.0f)) flo = 0.0f;
+  const float f0 = (float)first, last = (float)last_i;
+  if (!(flo >= f0)) flo = f0;
   if (!(fhi <= last)) fhi = last;
-  if (flo > last || fhi < 0.0f || flo > fhi) { lo = 1; hi = 0; return; }
+  if (flo > last || fhi < f0 || flo > fhi) { lo = first + 1; hi = first; return; }
   lo = (int)flo;
   hi = (int)fhi;
 }
@@ -215,16 +216,20 @@ __global__ void __launch_bounds__(kFootprintBlock) k_preprocess(Ws w) {
       cy_lo = __fadd_rn(cy_lo, e);
     }
 
-    int x0 = 1, x1 = 0, y0 = 1, y1 = 0;
+    // the window in image coordinates, clamped to the rendered rows
+    // row0 .. row0 + out_h - 1 (a band of the image, or all of it)
+    int x0 = 1, x1 = 0, y0 = D.row0 + 1, y1 = D.row0;
     if (ok) {
       if (D.trunc_k > 0.0f) {
         const bool ratio = (D.flags & kFlagRatio) != 0;
-        window_axis(wcx, sx, D.lr_w, s, D.trunc_k, ratio, D.out_w, x0, x1);
-        window_axis(wcy, sy, D.lr_h, s, D.trunc_k, ratio, D.out_h, y0, y1);
+        window_axis(wcx, sx, D.lr_w, s, D.trunc_k, ratio, 0, D.out_w - 1, x0, x1);
+        window_axis(wcy, sy, D.lr_h, s, D.trunc_k, ratio, D.row0, D.row0 + D.out_h - 1, y0, y1);
       } else {
-        x0 = 0; x1 = D.out_w - 1; y0 = 0; y1 = D.out_h - 1;
+        x0 = 0; x1 = D.out_w - 1; y0 = D.row0; y1 = D.row0 + D.out_h - 1;
       }
     }
+    // Records and compact windows stay in image coordinates; tiles are the
+    // output's (rows from row0).
 
     // Exponent in HR pixels and log2 units: -q/2 of Eq. 2 times log2(e), with
     // u = X/s, v = Y/s, written with the square completed in X so that no
@@ -267,7 +272,7 @@ __global__ void __launch_bounds__(kFootprintBlock) k_preprocess(Ws w) {
     uint4 tr = make_uint4(0u, 0u, 0u, 0u);
     if (x0 <= x1 && y0 <= y1) {
       const int tx0 = x0 >> w.tile_shift, tx1 = x1 >> w.tile_shift;
-      const int ty0 = y0 >> w.tile_shift, ty1 = y1 >> w.tile_shift;
+      const int ty0 = (y0 - D.row0) >> w.tile_shift, ty1 = (y1 - D.row0) >> w.tile_shift;
       const uint32_t tw = (uint32_t)(tx1 - tx0 + 1), th = (uint32_t)(ty1 - ty0 + 1);
       cnt = tw * th;
       tr = make_uint4((uint32_t)(D.t_base + ty0 * D.tiles_x + tx0), (uint32_t)D.tiles_x, tw, th);

@@ -54,7 +54,7 @@ __device__ __forceinline__ void tile_origin(const Ws& w, int t, const ImageDesc*
   const int ty = lt / D->tiles_x;
   const int tx = lt - ty * D->tiles_x;
   ox = tx * TILE;
-  oy = ty * TILE;
+  oy = ty * TILE + D->row0;   // image rows (the output holds rows row0 ..)
 }
 
 // Copy the records of batch entries t, t + NT, ... (ids in gid[]) to raw.
@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(TILE * TILE / BY) k_raster_fwd(Ws w, const uin
     const int64_t plane = (int64_t)H * W;
 #pragma unroll
     for (int k = 0; k < BY; ++k) {
-      const int y = oy + row0 + k;
+      const int y = oy - D->row0 + row0 + k;   // output row
       if (y < H) {
         const int64_t o = (int64_t)y * W + x;
         const int j = k / 2;
@@ -511,7 +511,7 @@ __global__ void __launch_bounds__(TILE * TILE / BY) k_raster_bwd(Ws w, const uin
     const int64_t plane = (int64_t)H * W;
 #pragma unroll
     for (int k = 0; k < BY; ++k) {
-      const int y = oy + row0 + k;
+      const int y = oy - D->row0 + row0 + k;   // output row
       const bool in = x < W && y < H;
       const int64_t o = (int64_t)y * W + x;
       float* gk = reinterpret_cast<float*>(&g[k / 2][0]) + (k & 1);

@@ -40,7 +40,8 @@ class View:
     LR grid at scale s (Eq. 4). window: WINDOW_SIGMA (|x/s - mu| <= k sigma,
     k = trunc_k) or WINDOW_RATIO (Algorithm 1, ratio r = trunc_k); norm:
     NORM_DENSITY (Eq. 2) or NORM_PEAK; align: ALIGN_EQ4 (x samples x / s) or
-    ALIGN_HALF ((x + 1/2) / s - 1/2)."""
+    ALIGN_HALF ((x + 1/2) / s - 1/2). row0: the first image row the output
+    holds (a horizontal band of out_h rows; 0 for the whole image)."""
     lr_h: int
     lr_w: int
     out_h: int
@@ -50,6 +51,7 @@ class View:
     norm: int = 0
     window: int = 0
     align: int = 0
+    row0: int = 0
 
 
 def out_size(lr: int, scale: float) -> int:
@@ -114,7 +116,8 @@ def _struct_v(v, tile: int = 0, batch: int = 0, adjoint: int = 0) -> _abi.GsView
     return _abi.GsView(int(v.lr_h), int(v.lr_w), int(v.out_h), int(v.out_w), float(v.scale),
                        float(getattr(v, "trunc_k", 3.0)), int(getattr(v, "norm", 0)),
                        int(tile), int(batch), int(getattr(v, "window", 0)),
-                       int(getattr(v, "align", 0)), int(adjoint), int(getattr(v, "binning", 0)), 0)
+                       int(getattr(v, "align", 0)), int(adjoint), int(getattr(v, "binning", 0)),
+                       int(getattr(v, "row0", 0)))
 
 
 def _arrays(gs: Sequence[Gaussians], views, tile=0, batch=0):

@@ -1,10 +1,17 @@
-"""Image-level sharding for several GPUs: one process per GPU.
+"""Sharding for several GPUs: one process per GPU.
 
-Images of a batch are independent (own Gaussians, size and scale), so a
+Batches: images are independent (own Gaussians, size and scale), so a
 multi-GPU render partitions the images across ranks and needs no collective on
 the data path; the only communication is the host-side max of the timings.
-Images are assigned longest-first (by HR pixels x mean footprint proxy) to the
-least-loaded rank, which keeps uneven batches balanced.
+Images are assigned longest-first (by HR pixels) to the least-loaded rank,
+which keeps uneven batches balanced.
+
+One large image: its HR rows are split into horizontal bands, one per rank
+(`gs_view.row0`). Each rank renders its band from all the Gaussians: the
+forward needs no exchange (the bands are the image's rows, bit for bit when
+each band starts on a tile row). The adjoint of a band is the gradient of the
+loss restricted to its rows, so the image's gradient is the sum of the bands':
+one all-reduce of the N x 9 gradients (`allreduce_band_grads`).
 """
 from __future__ import annotations
 
@@ -42,3 +49,38 @@ def max_over_ranks(value: float, device=None) -> float:
                      device=device if device is not None else "cpu")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def band_rows(out_h: int, parts: int, tile: int = 16) -> list[tuple[int, int]]:
+    """Split out_h rows into `parts` bands (row0, rows) starting on tile rows
+    (so that every band renders its rows exactly as the whole image does),
+    as even as the tile rows allow; bands may be empty when there are fewer
+    tile rows than parts."""
+    if parts < 1 or tile < 1 or out_h < 0:
+        raise ValueError("need parts >= 1, tile >= 1, out_h >= 0")
+    trows = -(-out_h // tile)
+    bands = []
+    for p in range(parts):
+        t0, t1 = (trows * p) // parts, (trows * (p + 1)) // parts
+        r0, r1 = min(out_h, t0 * tile), min(out_h, t1 * tile)
+        bands.append((r0, r1 - r0))
+    return bands
+
+
+def band_view(view, row0: int, rows: int):
+    """A copy of `view` restricted to image rows row0 .. row0 + rows - 1."""
+    import copy
+    v = copy.copy(view)
+    v.out_h = rows
+    v.row0 = row0
+    return v
+
+
+def allreduce_band_grads(grads):
+    """Sum a band's parameter gradients over the ranks of the default process
+    group (in place; the image's gradient on every rank). Identity without a
+    process group."""
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.all_reduce(grads, op=dist.ReduceOp.SUM)
+    return grads
