@@ -171,9 +171,10 @@ typedef struct gs_view {
   int32_t row0;         /* first image row this view renders (0: the whole image). The output
                            holds rows row0 .. row0 + out_h - 1 of the image: a horizontal band,
                            with row0 + out_h <= floor(s * lr_h) + 1. Windows and exponents are
-                           those of the whole image, so the bands of a partition render the same
-                           pixels bit for bit and their adjoints sum to the whole image's (the
-                           row split of one image over several devices, one sum of the
+                           those of the whole image, so a band renders the image's rows (bit for
+                           bit when row0 is a multiple of the tile, else to float32 rounding),
+                           and the adjoints of the bands of a partition sum to the whole image's
+                           (the row split of one image over several devices, one sum of the
                            gradients). */
 } gs_view;
 
