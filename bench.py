@@ -54,11 +54,11 @@ PAIR_CYCLES = {"raster_fwd": 6.5, "raster_bwd": 12.0, "raster_bwd_gw": 12.0}
 # DRAM bytes (read + write) of one launch of the dominant kernel, from one ncu
 # capture per workload (summaries under profiles/), valid only for the raster
 # source they were taken on: reported as null once gs_raster.cu changes.
-TRAFFIC_SRC_SHA256 = "ab0b47528b5c15c6e5830ef053d774152ab303e62be1b08344f0eb1504b6ba10"
-TRAFFIC = {("c2", "raster_bwd"): (21317376 + 0, "profiles/raster_bwd_c2_1024x1024.md"),
-           ("c4x12-bf16", "raster_bwd"): (346413312 + 23498240,
+TRAFFIC_SRC_SHA256 = "2f73061372f2f4ffe6fa8129874a30abb99528d14d6ff8309b6b817d75a10210"
+TRAFFIC = {("c2", "raster_bwd"): (21317120 + 0, "profiles/raster_bwd_c2_1024x1024.md"),
+           ("c4x12-bf16", "raster_bwd"): (346431744 + 23523328,
                                           "profiles/raster_bwd_c4x12_bf16_5760x3240.md"),
-           ("c4x12-bf16", "raster_fwd"): (37811968 + 233567488,
+           ("c4x12-bf16", "raster_fwd"): (37893120 + 233324032,
                                           "profiles/raster_fwd_c4x12_bf16_5760x3240.md")}
 
 
