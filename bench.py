@@ -355,18 +355,55 @@ def run_gpu(args, rank, world, local_rank):
     # synchronisation, and always the last). Events between the chained kernels
     # stop the next launch from overlapping the previous one's drain.
     every = max(1, args.kernel_every)
-    for k in range(args.steps):
-        flush.zero_()
-        gs.timing_enable(timed_kernels if k % every == every - 1 or k == args.steps - 1 else [])
-        ev[k][0].record(stream)
-        plan.fwd(stream)
-        if with_adj:
-            plan.bwd(stream)
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
-    launches = gs.launch_count() - launches0
-    gs.timing_enable([])
-    ktimes = gs.timing_read()
+    use_graph = args.graph if args.graph is not None else args.workload in ("c3", "c3eq")
+    if use_graph:
+        # the whole step as one CUDA graph (captured once, replayed per step);
+        # the dominant kernel's events are the graph's event-record nodes, read
+        # after each replay
+        cap = torch.cuda.Stream()
+        cap.wait_stream(stream)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        l0 = gs.launch_count()
+        gs.timing_enable(timed_kernels)
+        with torch.cuda.graph(graph, stream=cap):
+            plan.fwd(torch.cuda.current_stream())
+            if with_adj:
+                plan.bwd(torch.cuda.current_stream())
+        gs.timing_enable([])
+        launches_per_step = gs.launch_count() - l0
+        for _ in range(2):
+            flush.zero_()
+            graph.replay()
+        torch.cuda.synchronize()
+        gs.timing_read()
+        ktimes = {}
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            graph.replay()
+            ev[k][1].record(stream)
+            ev[k][1].synchronize()
+            for kk, (ms, cnt) in gs.timing_read().items():
+                a0, c0 = ktimes.get(kk, (0.0, 0))
+                ktimes[kk] = (a0 + ms, c0 + cnt)
+        torch.cuda.synchronize()
+        gs.timing_release()
+        del graph
+        launches = launches_per_step * args.steps
+    else:
+        for k in range(args.steps):
+            flush.zero_()
+            gs.timing_enable(timed_kernels if k % every == every - 1 or k == args.steps - 1 else [])
+            ev[k][0].record(stream)
+            plan.fwd(stream)
+            if with_adj:
+                plan.bwd(stream)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        launches = gs.launch_count() - launches0
+        gs.timing_enable([])
+        ktimes = gs.timing_read()
     timed_ktimes = dict(ktimes)
     if world > 1:
         dist.barrier()
@@ -460,6 +497,7 @@ def run_gpu(args, rank, world, local_rank):
                                                            ("tile", "batch", "binning", "ms",
                                                             "from_cache", "n_timed")},
                    "adjoint": "gaussian-warp" if plan.V[0].adjoint == 2 else "tile",
+                   "cuda_graph": bool(use_graph),
                    "hr_pixels_per_step": hr_pix, "gaussians": sum(g.n for g in dgs),
                    "parallelism": f"replicas x{world} (one full workload per GPU)"},
         "fwd_mpix_s": round(hr_pix * args.steps / (sum(fwd_ms) * 1e-3) / 1e6, 2),
@@ -935,6 +973,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-probe", action="store_true", help="skip the unit-throughput probe")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--graph", dest="graph", action="store_true", default=None,
+                    help="time each step as one CUDA-graph replay (default for c3 / c3eq)")
+    ap.add_argument("--no-graph", dest="graph", action="store_false")
     ap.add_argument("--kernel-every", type=int, default=1,
                     help="bracket the dominant kernel with CUDA events on every k-th timed step "
                          "(1: every step; sparser brackets leave more steps with overlapped "

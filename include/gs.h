@@ -270,14 +270,18 @@ const char* gs_status_string(int32_t status);
 int64_t gs_launch_count(void);
 
 /* Per-kernel timing with CUDA events recorded around each launch on the
- * launching stream (off by default; not for use under stream capture).
- * kernel_mask: bit k times kernel id k (see gs_kernel_name); 0 turns timing
- * off, -1 times every kernel. gs_timing_read synchronises the recorded events,
- * adds each kernel's time since the last read into ms_out[k] and its launches
- * into count_out[k] for k < n, returns the number of kernel ids, and clears the
- * record. */
+ * launching stream (off by default). kernel_mask: bit k times kernel id k (see
+ * gs_kernel_name); 0 turns timing off, -1 times every kernel. gs_timing_read
+ * synchronises the recorded events, adds each kernel's time since the last
+ * read into ms_out[k] and its launches into count_out[k] for k < n, returns
+ * the number of kernel ids, and clears the record. Launches made under stream
+ * capture record their events as the graph's event-record nodes: every replay
+ * records them again, gs_timing_read adds the last replay's times (none before
+ * the first replay) and keeps them for the next read, and gs_timing_release
+ * drops them (call it before destroying the graph). */
 gs_status gs_timing_enable(int32_t kernel_mask);
 int32_t gs_timing_read(double* ms_out, int64_t* count_out, int32_t n);
+gs_status gs_timing_release(void);
 const char* gs_kernel_name(int32_t id);
 
 /* Measured throughputs of the units that bound the raster kernels. */

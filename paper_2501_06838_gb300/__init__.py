@@ -8,12 +8,12 @@ PyTorch binding.
 """
 from ._abi import GsError, load as load_library  # noqa: F401
 from .render import (Gaussians, GSRender, GSRenderBatched, Plan, View, Workspace, count_pairs,  # noqa: F401
-                     launch_count, timing_enable, timing_read, make_workspace, read_stats, render, render_batched,
+                     launch_count, timing_enable, timing_read, timing_release, make_workspace, read_stats, render, render_batched,
                      render_batched_bwd, render_bwd, render_single_bwd, render_single_fwd,
                      out_size, sync_status, workspace_bytes)
 
 __all__ = ["Gaussians", "GSRender", "GSRenderBatched", "Plan", "View", "Workspace", "timing_enable",
-           "timing_read", "GsError", "count_pairs",
+           "timing_read", "timing_release", "GsError", "count_pairs",
            "launch_count", "load_library", "make_workspace", "read_stats", "render",
            "render_batched", "render_batched_bwd", "render_bwd", "render_single_bwd",
            "render_single_fwd", "out_size", "sync_status", "workspace_bytes"]

@@ -25,8 +25,8 @@ GS_BINNING_AUTO, GS_BINNING_SORT, GS_BINNING_GRID = 0, 1, 2
 EXPORTS = ("gs_workspace_size", "gs_count_pairs", "gs_render_fwd", "gs_render_bwd",
            "gs_render_batched", "gs_render_batched_bwd", "gs_sync_status", "gs_read_stats",
            "gs_last_error", "gs_status_string", "gs_launch_count", "gs_timing_enable",
-           "gs_timing_read", "gs_kernel_name", "gs_version", "gs_render_fwd_noalloc",
-           "gs_probe_peaks", "gs_tune")
+           "gs_timing_read", "gs_timing_release", "gs_kernel_name", "gs_version",
+           "gs_render_fwd_noalloc", "gs_probe_peaks", "gs_tune")
 
 
 class GsHead(ctypes.Structure):
@@ -113,6 +113,7 @@ def load(path: str | None = None):
             "gs_launch_count": (i64, []),
             "gs_timing_enable": (i32, [i32]),
             "gs_timing_read": (i32, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64), i32]),
+            "gs_timing_release": (i32, []),
             "gs_kernel_name": (ctypes.c_char_p, [i32]),
             "gs_version": (ctypes.c_char_p, []),
             "gs_render_fwd_noalloc": (i32, [G, V, vp, vp]),

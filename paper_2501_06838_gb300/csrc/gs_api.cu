@@ -32,6 +32,7 @@ std::atomic<int64_t> g_launches{0};
 struct TimedLaunch {
   int id;
   cudaEvent_t a, b;
+  bool graph;   // recorded under stream capture: event-record nodes, re-recorded by every replay
 };
 std::mutex g_tmu;
 std::atomic<uint32_t> g_timing_mask{0u};
@@ -437,12 +438,19 @@ bool chain_overlap() {
   return on;
 }
 
+namespace {
+bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(s, &st) == cudaSuccess && st == cudaStreamCaptureStatusActive;
+}
+}  // namespace
+
 void launch_begin(int id, cudaStream_t s) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
   if (!((g_timing_mask.load(std::memory_order_relaxed) >> id) & 1u)) return;
   std::lock_guard<std::mutex> lk(g_tmu);
   cudaEvent_t a = take_event();
-  if (a) cudaEventRecord(a, s);
+  if (a) cudaEventRecordWithFlags(a, s, capturing(s) ? cudaEventRecordExternal : cudaEventRecordDefault);
   g_pending_start = a;
 }
 
@@ -454,8 +462,9 @@ void launch_end(int id, cudaStream_t s) {
   if (!a) return;
   cudaEvent_t b = take_event();
   if (!b) { g_event_pool.push_back(a); return; }
-  cudaEventRecord(b, s);
-  g_timed.push_back(TimedLaunch{id, a, b});
+  const bool cap = capturing(s);
+  cudaEventRecordWithFlags(b, s, cap ? cudaEventRecordExternal : cudaEventRecordDefault);
+  g_timed.push_back(TimedLaunch{id, a, b, cap});
 }
 
 }  // namespace gs
@@ -577,18 +586,40 @@ gs_status gs_timing_enable(int32_t kernel_mask) {
 
 int32_t gs_timing_read(double* ms_out, int64_t* count_out, int32_t n) {
   std::lock_guard<std::mutex> lk(g_tmu);
+  std::vector<TimedLaunch> keep;
   for (const TimedLaunch& t : g_timed) {
     cudaEventSynchronize(t.b);
     float ms = 0.0f;
     if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess && t.id < n) {
       if (ms_out) ms_out[t.id] += ms;
       if (count_out) count_out[t.id] += 1;
+    } else {
+      cudaGetLastError();   // a captured pair not yet replayed: no time to add
     }
-    g_event_pool.push_back(t.a);
-    g_event_pool.push_back(t.b);
+    if (t.graph) {
+      keep.push_back(t);
+    } else {
+      g_event_pool.push_back(t.a);
+      g_event_pool.push_back(t.b);
+    }
   }
-  g_timed.clear();
+  g_timed.swap(keep);
   return kKNumKernels;
+}
+
+gs_status gs_timing_release(void) {
+  std::lock_guard<std::mutex> lk(g_tmu);
+  std::vector<TimedLaunch> keep;
+  for (const TimedLaunch& t : g_timed) {
+    if (t.graph) {
+      g_event_pool.push_back(t.a);
+      g_event_pool.push_back(t.b);
+    } else {
+      keep.push_back(t);
+    }
+  }
+  g_timed.swap(keep);
+  return GS_OK;
 }
 
 const char* gs_kernel_name(int32_t id) {

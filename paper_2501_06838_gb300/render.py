@@ -391,6 +391,11 @@ def timing_read() -> dict:
     return {lib.gs_kernel_name(i).decode(): (ms[i], cnt[i]) for i in range(n) if cnt[i]}
 
 
+def timing_release():
+    """Drop the timed launches recorded under stream capture (before the graph goes)."""
+    _abi.check(_abi.load().gs_timing_release(), "gs_timing_release")
+
+
 def probe_peaks() -> dict:
     """Measured FFMA / FFMA2 / MUFU.EX2 rates and the forward pair mix (per
     second and per SM per clock at the device's maximum clock)."""

@@ -47,6 +47,37 @@ def test_config3_batched_forward_and_graph():
     plan.status()
 
 
+def test_kernel_timing_under_graph_capture():
+    """Launches timed under stream capture record the graph's event nodes:
+    every replay re-records them, each read gives the last replay's times."""
+    import torch
+    import paper_2501_06838_gb300 as gs
+    gsets, views = S.config3(4)
+    dgs = [device_gaussians(g) for g in gsets]
+    plan = gs.Plan(dgs, views, with_grads=False)
+    plan.fwd()
+    torch.cuda.synchronize()
+    gs.timing_read()
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    gs.timing_enable(["raster_fwd"])
+    with torch.cuda.graph(graph, stream=stream):
+        plan.fwd(stream)
+    gs.timing_enable([])
+    assert gs.timing_read() == {}          # nothing replayed yet
+    for _ in range(3):
+        graph.replay()
+        torch.cuda.synchronize()
+        kt = gs.timing_read()
+        assert kt["raster_fwd"][1] == 1 and kt["raster_fwd"][0] > 0.0
+    gs.timing_release()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert gs.timing_read() == {}
+    plan.status()
+
+
 def test_batched_equals_single_image_calls():
     import torch
     import paper_2501_06838_gb300 as gs
