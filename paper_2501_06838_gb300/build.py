@@ -7,6 +7,7 @@ internal header or include/gs.h is newer than the library.
 from __future__ import annotations
 
 import concurrent.futures as cf
+import fcntl
 import glob
 import os
 import shutil
@@ -52,28 +53,42 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if not force and not _stale(LIB, srcs + headers + [__file__]):
             return LIB
         os.makedirs(BUILD, exist_ok=True)
-        cc = nvcc()
+        # one builder at a time across processes (several ranks start together)
+        with open(os.path.join(BUILD, ".lock"), "w") as lk:
+            fcntl.flock(lk, fcntl.LOCK_EX)
+            try:
+                if not force and not _stale(LIB, srcs + headers + [__file__]):
+                    return LIB
+                return _build_locked(srcs, headers, force, verbose)
+            finally:
+                fcntl.flock(lk, fcntl.LOCK_UN)
 
-        def compile_one(src):
-            obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-            if force or _stale(obj, [src] + headers + [__file__]):
-                cmd = [cc, *ARCH, *FLAGS, "-c", src, "-o", obj]
-                r = subprocess.run(cmd, capture_output=True, text=True)
-                if r.returncode != 0:
-                    raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
-                if verbose and (r.stdout or r.stderr):
-                    print(r.stdout, r.stderr)
-            return obj
 
-        with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
-            objs = list(ex.map(compile_one, srcs))
-        tmp = LIB + f".{os.getpid()}.tmp"
-        cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs]
-        r = subprocess.run(cmd, capture_output=True, text=True)
-        if r.returncode != 0:
-            raise RuntimeError(f"link of libgs.so failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
-        return LIB
+def _build_locked(srcs, headers, force, verbose) -> str:
+    cc = nvcc()
+
+    def compile_one(src):
+        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        if force or _stale(obj, [src] + headers + [__file__]):
+            tmp_obj = obj + f".{os.getpid()}.tmp"
+            cmd = [cc, *ARCH, *FLAGS, "-c", src, "-o", tmp_obj]
+            r = subprocess.run(cmd, capture_output=True, text=True)
+            if r.returncode != 0:
+                raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
+            if verbose and (r.stdout or r.stderr):
+                print(r.stdout, r.stderr)
+            os.replace(tmp_obj, obj)
+        return obj
+
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
+        objs = list(ex.map(compile_one, srcs))
+    tmp = LIB + f".{os.getpid()}.tmp"
+    cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link of libgs.so failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, LIB)
+    return LIB
 
 
 if __name__ == "__main__":
