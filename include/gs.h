@@ -321,8 +321,8 @@ typedef struct gs_tuning {
  * gs_workspace_size(..., cap) for cap = gs_count_pairs at tile 8 (the most
  * pairs). outs / grads are overwritten by the timed calls. Synchronous.
  *
- * cache_path (may be NULL): a text file of lines
- *   "<signature> <tile> <batch> <binning> <adjoint> <ms>",
+ * cache_path (may be NULL): a JSON-lines file, one object per tuned workload,
+ *   {"signature": "...", "tile": T, "batch": B, "binning": N, "adjoint": A, "ms": t},
  * the signature being the device name, parameter dtype, fwd or fwd+bwd, and
  * the log2 size classes of the HR pixels, the images and the pairs per pixel.
  * A matching line is returned without timing (from_cache = 1); a new result is

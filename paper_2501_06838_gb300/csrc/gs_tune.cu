@@ -1,7 +1,7 @@
 // Autotuner of the render's launch parameters (tile edge, shared-memory batch,
 // binning), behind gs_tune in include/gs.h. Host code: it times the public
 // entry points with CUDA events on the caller's workload and keeps the
-// fastest choice per workload signature in an optional text cache.
+// fastest choice per workload signature in an optional JSON-lines cache.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -42,16 +42,26 @@ std::string signature(int32_t n_images, const gs_gaussians* g, const gs_view* v,
   return buf;
 }
 
+// The cache is JSON lines, one object per tuned workload:
+//   {"signature": "...", "tile": 16, "batch": 32, "binning": 2, "adjoint": 1, "ms": 0.125}
+// (written by cache_append; other lines are skipped).
 bool cache_lookup(const char* path, const std::string& sig, gs_tuning* out) {
   if (!path) return false;
   FILE* f = std::fopen(path, "r");
   if (!f) return false;
-  char key[256];
+  char line[512], key[256];
   gs_tuning t{};
   bool found = false;
-  while (std::fscanf(f, "%255s %d %d %d %d %f", key, &t.tile, &t.batch, &t.binning, &t.adjoint,
-                     &t.ms) == 6)
-    if (sig == key) { *out = t; found = true; }   // the last matching line wins
+  while (std::fgets(line, sizeof(line), f)) {
+    if (std::sscanf(line,
+                    " {\"signature\": \"%255[^\"]\", \"tile\": %d, \"batch\": %d, "
+                    "\"binning\": %d, \"adjoint\": %d, \"ms\": %f}",
+                    key, &t.tile, &t.batch, &t.binning, &t.adjoint, &t.ms) == 6 &&
+        sig == key) {
+      *out = t;   // the last matching line wins
+      found = true;
+    }
+  }
   std::fclose(f);
   return found;
 }
@@ -60,7 +70,10 @@ void cache_append(const char* path, const std::string& sig, const gs_tuning& t) 
   if (!path) return;
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "%s %d %d %d %d %.6f\n", sig.c_str(), t.tile, t.batch, t.binning, t.adjoint, t.ms);
+  std::fprintf(f,
+               "{\"signature\": \"%s\", \"tile\": %d, \"batch\": %d, \"binning\": %d, "
+               "\"adjoint\": %d, \"ms\": %.6f}\n",
+               sig.c_str(), t.tile, t.batch, t.binning, t.adjoint, t.ms);
   std::fclose(f);
 }
 

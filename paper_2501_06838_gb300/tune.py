@@ -2,7 +2,7 @@
 Gaussians per shared-memory batch, binning): a thin binding of the library's
 gs_tune, which times every candidate on the caller's own workload with CUDA
 events (median of `reps` calls after two warm-up calls), returns the fastest
-and keeps it in a text cache keyed by the workload's signature (device, dtype,
+and keeps it in a JSON-lines cache keyed by the workload's signature (device, dtype,
 fwd or fwd+bwd, and the log2 size classes of HR pixels, images and pairs per
 pixel).
 """
@@ -21,7 +21,7 @@ _BINNING = {_abi.GS_BINNING_SORT: "sort", _abi.GS_BINNING_GRID: "grid"}
 
 def default_cache() -> str:
     return os.environ.get("GS_TUNE_CACHE",
-                          os.path.join(os.path.expanduser("~"), ".cache", "gs_tune.txt"))
+                          os.path.join(os.path.expanduser("~"), ".cache", "gs_tune.jsonl"))
 
 
 def tune(gs, views, with_grads: bool = True, reps: int = 5, cache: str | None = None,

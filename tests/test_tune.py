@@ -15,12 +15,17 @@ def test_tune_picks_and_caches(tmp_path):
     from paper_2501_06838_gb300.tune import tune
     gsets, views = S.config3(n_images=4)
     dgs = [device_gaussians(g) for g in gsets]
-    cache = str(tmp_path / "tune.txt")
+    cache = str(tmp_path / "tune.jsonl")
     e1 = tune(dgs, views, with_grads=True, reps=3, cache=cache)
     assert e1["tile"] in (8, 16, 32) and e1["binning"] in ("sort", "grid")
     assert not e1["from_cache"] and e1["n_timed"] == 12 and e1["ms"] > 0
+    import json
     with open(cache) as f:
-        assert len(f.read().splitlines()) == 1
+        lines = f.read().splitlines()
+    assert len(lines) == 1
+    rec = json.loads(lines[0])
+    assert (rec["tile"], rec["batch"]) == (e1["tile"], e1["batch"]) and rec["ms"] > 0
+    assert rec["signature"].count("|") >= 5
     e2 = tune(dgs, views, with_grads=True, reps=3, cache=cache)
     assert e2["from_cache"] and (e2["tile"], e2["batch"], e2["binning"]) == \
         (e1["tile"], e1["batch"], e1["binning"])
