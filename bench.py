@@ -17,6 +17,7 @@ the events. Under torchrun every rank renders its own copy of the workload
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -847,8 +848,7 @@ def oracle_step(gsets, views, with_adj, band=None, threads=0, grad_outs=None):
     import oracle
     outs, grads, px = [], [], 0
     for i, (g, v) in enumerate(zip(gsets, views)):
-        vv = v if band is None else S.View(v.lr_h, v.lr_w, min(band, v.out_h), v.out_w, v.scale,
-                                           v.trunc_k, v.norm)
+        vv = v if band is None else dataclasses.replace(v, out_h=min(band, v.out_h))
         outs.append(oracle.render(g, vv, threads=threads))
         if with_adj:
             go = grad_outs[i] if grad_outs is not None else S.grad_out(1, v.out_h, v.out_w)
@@ -894,6 +894,15 @@ def run_cpu_baseline(gsets, views, with_adj, plan, seconds):
     cb = {"value": round(px / t / 1e6, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
           "sample": sample + (" (fwd + adjoint)" if with_adj else " (fwd)"),
           "seconds": round(t, 2)}
+    # the same oracle on one core, on a sample of about a tenth of the budget
+    band1 = sample_band(gsets, views, with_adj, seconds / 10 / max(cores, 1))
+    t1 = time.time()
+    _, _, px1 = oracle_step(gsets, views, with_adj, band=band1, threads=1)
+    t1 = time.time() - t1
+    cb["single_core"] = {"value": round(px1 / t1 / 1e6, 4), "cores": 1,
+                         "sample": ("one oracle step of the full workload" if band1 is None else
+                                    f"one oracle step on the top {band1} rows of every image"),
+                         "seconds": round(t1, 2)}
     # error of this run's GPU result against the oracle (on the same sample)
     err = {}
     try:
