@@ -63,6 +63,16 @@ def test_host_only_entry_points(lib):
     assert lib.gs_workspace_size(1, G, V, 0) == 0
     V[0].out_h = 193
     assert lib.gs_workspace_size(1, G, V, 0) > 0
+    # a row band: rows row0 .. row0 + out_h - 1 must lie within floor(s * lr_h) + 1
+    V[0].out_h, V[0].row0 = 64, 100
+    assert lib.gs_workspace_size(1, G, V, 0) > 0
+    V[0].row0 = 130
+    assert lib.gs_workspace_size(1, G, V, 0) == 0
+    assert b"larger than" in lib.gs_last_error()
+    V[0].row0 = -1
+    assert lib.gs_workspace_size(1, G, V, 0) == 0
+    assert b"row0" in lib.gs_last_error()
+    V[0].out_h, V[0].row0 = 192, 0
     V[0].scale = float("nan")
     assert lib.gs_workspace_size(1, G, V, 0) == 0
     assert lib.gs_launch_count() == 0
