@@ -631,7 +631,7 @@ def run_pipeline(args, rank, world, local_rank):
     import torch
 
     import paper_2501_06838_gb300 as gs
-    from paper_2501_06838_gb300.gsasr import GSASR
+    from paper_2501_06838_gb300.gsasr import GSASR, GSASRConfig
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     scale = PIPELINE_SCALES[args.workload]
@@ -639,7 +639,8 @@ def run_pipeline(args, rank, world, local_rank):
     h, w = lr_img.shape[1:]
     torch.backends.cudnn.benchmark = True    # fixed shapes: let cuDNN pick its conv kernels
     torch.manual_seed(0)
-    net = GSASR().to(dev, dtype=torch.bfloat16).eval()   # BF16 weights and activations
+    cfg = GSASRConfig(pad_width=getattr(args, "pipeline_width", "padded") == "padded")
+    net = GSASR(cfg).to(dev, dtype=torch.bfloat16).eval()   # BF16 weights and activations
     lr_t = torch.from_numpy(lr_img)[None].to(dev)
     scales = torch.full((1,), float(scale), device=dev)
     hr_pix = S.out_size(h, scale) * S.out_size(w, scale)
@@ -705,6 +706,7 @@ def run_pipeline(args, rank, world, local_rank):
             "dtype": "bf16 network, render from bf16 raw outputs in f32", "data": "synthetic (random weights)",
             "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}",
                        "lr": [h, w], "gaussians": net.cfg.m * h * w, "hr_pixels_per_step": hr_pix,
+                       "d": net.cfg.d, "d_stored": net.cfg.d_store,
                        "l2": "flushed before every step; the decoder's activations are GBs"},
             "stage_ms": {"encoder": round(stages[0] / args.steps, 3),
                          "decoder": round(stages[1] / args.steps, 3),
@@ -990,6 +992,8 @@ def main():
                          "(1: every step; sparser brackets leave more steps with overlapped "
                          "launches, but the bracketed launches then measured ~5%% longer)")
     ap.add_argument("--ref-step-seconds", type=float, default=3.0)
+    ap.add_argument("--pipeline-width", choices=["padded", "real"], default="padded",
+                    help="gsasr-x*: hold the decoder's d = 180 at 184 (aligned GEMM rows) or not")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -66,6 +66,16 @@ class GSASRConfig:
     mlp_ratio: int = 2         # MLP hidden width / d
     scale_tokens: int = 8      # tokens the scale cross-attention attends to
     window_chunk: int = 32     # windows per attention call (bounds temporaries)
+    pad_width: bool = True     # hold the width-d stream at a multiple of 8
+
+    @property
+    def d_store(self) -> int:
+        """Width the embeddings are held at: d rounded up to a multiple of 8, so
+        that every GEMM of the decoder has 16-byte aligned rows in BF16; d itself
+        with pad_width off. The extra channels of the residual stream carry the
+        mean of the real ones, which makes the layer norms exact (_PLayerNorm);
+        every other extra channel is zero and every layer ignores them."""
+        return -(-self.d // 8) * 8 if self.pad_width else self.d
 
 
 @dataclass
@@ -194,23 +204,74 @@ class EDSRBaseline(nn.Module):
         return h + self.tail(self.body(h))
 
 
+class _PLinear(nn.Linear):
+    """nn.Linear(in_real -> out_real) held at widths (in_store, out_store).
+    The extra input columns are zero, so extra input channels are ignored.
+    The extra output rows are zero (pad="zero"), or each is the mean of the
+    real rows (pad="mean"), so that every extra output equals the mean of the
+    real outputs. Initialised as the real layer."""
+
+    def __init__(self, in_real: int, out_real: int, in_store: int = 0, out_store: int = 0,
+                 pad: str = "zero"):
+        super().__init__(in_store or in_real, out_store or out_real)
+        self.in_real, self.out_real, self.pad = in_real, out_real, pad
+        if (self.in_features, self.out_features) != (in_real, out_real):
+            ref = nn.Linear(in_real, out_real)
+            with torch.no_grad():
+                self.weight.zero_()
+                self.bias.zero_()
+                self.weight[:out_real, :in_real] = ref.weight
+                self.bias[:out_real] = ref.bias
+            self.sync_pads()
+
+    @torch.no_grad()
+    def sync_pads(self):
+        """Re-derive the extra rows and columns from the real block."""
+        r, c = self.out_real, self.in_real
+        self.weight[:, c:] = 0
+        fill_w = self.weight[:r].mean(0) if self.pad == "mean" else 0
+        fill_b = self.bias[:r].mean() if self.pad == "mean" else 0
+        self.weight[r:] = fill_w
+        self.bias[r:] = fill_b
+
+
+class _PLayerNorm(nn.LayerNorm):
+    """LayerNorm over d_real channels held at d_store, for an input whose extra
+    channels each carry the mean m of the real ones (the residual stream of
+    this model, whose producers are pad="mean" layers). Then the d_store-wide
+    statistics are m and (d_real / d_store) var, so a LayerNorm of width d_store
+    with eps and the real weights both scaled by d_real / d_store (the weights
+    by its square root) gives the d_real-wide LayerNorm on the real channels,
+    exactly; its extra outputs are zero (zero weight and bias there)."""
+
+    def __init__(self, d_real: int, d_store: int = 0, eps: float = 1e-5):
+        c = d_real / float(d_store or d_real)
+        super().__init__(d_store or d_real, eps=eps * c)
+        self.d_real, self.gain = d_real, math.sqrt(c)
+        with torch.no_grad():
+            self.weight[:d_real] = self.gain
+            self.weight[d_real:] = 0
+            self.bias[d_real:] = 0
+
+
 class _Attention(nn.Module):
     """Multi-head attention with queries from x and keys / values from ctx,
     heads padded from d / heads to head_pad columns (zero weights; the scale
     stays 1 / sqrt(d / heads))."""
 
-    def __init__(self, d: int, ctx_dim: int, heads: int, head_pad: int):
+    def __init__(self, d: int, ctx_dim: int, heads: int, head_pad: int, d_store: int = 0,
+                 ctx_store: int = 0):
         super().__init__()
         self.heads, self.hd, self.hp = heads, d // heads, head_pad
-        self.q = nn.Linear(d, heads * head_pad)
-        self.kv = nn.Linear(ctx_dim, 2 * heads * head_pad)
-        self.proj = nn.Linear(heads * head_pad, d)
+        self.q = _PLinear(d, heads * head_pad, d_store)
+        self.kv = _PLinear(ctx_dim, 2 * heads * head_pad, ctx_store)
+        self.proj = _PLinear(heads * head_pad, d, 0, d_store, pad="mean")
         with torch.no_grad():   # padded columns carry zeros
             for lin, rows in ((self.q, 1), (self.kv, 2)):
                 wv = lin.weight.view(rows * heads, head_pad, -1)
                 wv[:, self.hd:] = 0
                 lin.bias.view(rows * heads, head_pad)[:, self.hd:] = 0
-            self.proj.weight.view(d, heads, head_pad)[:, :, self.hd:] = 0
+            self.proj.weight.view(-1, heads, head_pad)[:, :, self.hd:] = 0
 
     def split(self, t, n):
         return t.view(t.shape[0], n, self.heads, self.hp).transpose(1, 2)
@@ -228,9 +289,10 @@ class _Attention(nn.Module):
 
 
 class _MLP(nn.Module):
-    def __init__(self, d: int, ratio: int):
+    def __init__(self, d: int, ratio: int, d_store: int = 0):
         super().__init__()
-        self.fc1, self.fc2 = nn.Linear(d, ratio * d), nn.Linear(ratio * d, d)
+        self.fc1 = _PLinear(d, ratio * d, d_store)
+        self.fc2 = _PLinear(ratio * d, d, 0, d_store, pad="mean")
 
     def forward(self, x):
         return self.fc2(F.gelu(self.fc1(x)))
@@ -244,12 +306,13 @@ class ConditionInjection(nn.Module):
         super().__init__()
         r = math.isqrt(cfg.m)
         self.cfg = cfg
-        self.ln_q, self.ln_f, self.ln_m = nn.LayerNorm(cfg.d), nn.LayerNorm(cfg.n_feats), \
-            nn.LayerNorm(cfg.d)
-        self.att = _Attention(cfg.d, cfg.n_feats, cfg.heads, cfg.head_pad)
+        dp = cfg.d_store
+        self.ln_q, self.ln_f, self.ln_m = _PLayerNorm(cfg.d, dp), nn.LayerNorm(cfg.n_feats), \
+            _PLayerNorm(cfg.d, dp)
+        self.att = _Attention(cfg.d, cfg.n_feats, cfg.heads, cfg.head_pad, dp)
         self.table = nn.Parameter(0.02 * torch.randn((2 * r * cfg.k) ** 2, cfg.heads))
         self.register_buffer("index", relative_index_cross(cfg.k, r), persistent=False)
-        self.mlp = _MLP(cfg.d, cfg.mlp_ratio)
+        self.mlp = _MLP(cfg.d, cfg.mlp_ratio, dp)
 
     def forward(self, e_base, feats, b, gh, gw):
         """e_base: [T, d]; feats: [B, Hp, Wp, C] -> token grid [B, gh, gw, d]."""
@@ -270,11 +333,12 @@ class _WindowSelfAttention(nn.Module):
         super().__init__()
         self.cfg, self.shift = cfg, shift
         self.w = math.isqrt(cfg.m) * cfg.k
-        self.ln, self.ln_m = nn.LayerNorm(cfg.d), nn.LayerNorm(cfg.d)
-        self.att = _Attention(cfg.d, cfg.d, cfg.heads, cfg.head_pad)
+        dp = cfg.d_store
+        self.ln, self.ln_m = _PLayerNorm(cfg.d, dp), _PLayerNorm(cfg.d, dp)
+        self.att = _Attention(cfg.d, cfg.d, cfg.heads, cfg.head_pad, dp, dp)
         self.table = nn.Parameter(0.02 * torch.randn((2 * self.w - 1) ** 2, cfg.heads))
         self.register_buffer("index", relative_index_self(self.w), persistent=False)
-        self.mlp = _MLP(cfg.d, cfg.mlp_ratio)
+        self.mlp = _MLP(cfg.d, cfg.mlp_ratio, dp)
 
     def forward(self, x):
         b, gh, gw, _ = x.shape
@@ -301,15 +365,16 @@ class _ScaleAttention(nn.Module):
     def __init__(self, cfg: GSASRConfig):
         super().__init__()
         self.cfg = cfg
+        dp = cfg.d_store
         self.embed = nn.Sequential(nn.Linear(32, cfg.d), nn.GELU(),
                                    nn.Linear(cfg.d, cfg.scale_tokens * cfg.d))
-        self.ln, self.ln_m = nn.LayerNorm(cfg.d), nn.LayerNorm(cfg.d)
-        self.att = _Attention(cfg.d, cfg.d, cfg.heads, cfg.head_pad)
-        self.mlp = _MLP(cfg.d, cfg.mlp_ratio)
+        self.ln, self.ln_m = _PLayerNorm(cfg.d, dp), _PLayerNorm(cfg.d, dp)
+        self.att = _Attention(cfg.d, cfg.d, cfg.heads, cfg.head_pad, dp)
+        self.mlp = _MLP(cfg.d, cfg.mlp_ratio, dp)
 
     def forward(self, x, scale_feat):
         b, gh, gw, d = x.shape
-        tok = self.embed(scale_feat).view(b, self.cfg.scale_tokens, d)
+        tok = self.embed(scale_feat).view(b, self.cfg.scale_tokens, self.cfg.d)
         o = self.att(self.ln(x).view(b, gh * gw, d), tok).view(b, gh, gw, d)
         x = x + o
         return x + self.mlp(self.ln_m(x))
@@ -334,10 +399,12 @@ class GaussianPrimaryHead(nn.Module):
     (offset 2, sigma 2, rho 1, colour 3, opacity 1)."""
     OUTS = (2, 2, 1, 3, 1)
 
-    def __init__(self, d: int):
+    def __init__(self, d: int, d_store: int = 0):
         super().__init__()
-        self.mlps = nn.ModuleList([nn.Sequential(nn.Linear(d, d), nn.ReLU(), nn.Linear(d, d),
-                                                 nn.ReLU(), nn.Linear(d, o)) for o in self.OUTS])
+        dp = d_store or d
+        self.mlps = nn.ModuleList([nn.Sequential(_PLinear(d, d, dp, dp), nn.ReLU(),
+                                                 _PLinear(d, d, dp, dp), nn.ReLU(),
+                                                 _PLinear(d, o, dp)) for o in self.OUTS])
 
     def forward(self, x):
         return torch.cat([f(x) for f in self.mlps], -1)
@@ -361,11 +428,46 @@ class GSASR(nn.Module):
         if r * r != cfg.m or cfg.d % cfg.heads or cfg.head_pad < cfg.d // cfg.heads:
             raise ValueError("m must be a square, heads must divide d, head_pad >= d / heads")
         self.encoder = EDSRBaseline(cfg.n_feats, cfg.n_resblocks)
-        self.e_base = nn.Parameter(0.02 * torch.randn((r * cfg.k) ** 2, cfg.d))
+        e = torch.zeros((r * cfg.k) ** 2, cfg.d_store)
+        e[:, :cfg.d] = 0.02 * torch.randn((r * cfg.k) ** 2, cfg.d)
+        e[:, cfg.d:] = e[:, :cfg.d].mean(1, keepdim=True)
+        self.e_base = nn.Parameter(e)
         self.inject = ConditionInjection(cfg)
         self.blocks = nn.ModuleList([GaussianInteraction(cfg) for _ in range(cfg.blocks)])
-        self.ln = nn.LayerNorm(cfg.d)
-        self.head = GaussianPrimaryHead(cfg.d)
+        self.ln = _PLayerNorm(cfg.d, cfg.d_store)
+        self.head = GaussianPrimaryHead(cfg.d, cfg.d_store)
+
+    @torch.no_grad()
+    def sync_pads(self):
+        """Restore the extra channels of the width-d_store layers from the real
+        ones (needed after the real weights change)."""
+        d = self.cfg.d
+        self.e_base[:, d:] = self.e_base[:, :d].mean(1, keepdim=True)
+        for mod in self.modules():
+            if isinstance(mod, _PLinear):
+                mod.sync_pads()
+            elif isinstance(mod, _PLayerNorm):
+                mod.weight[mod.d_real:] = 0
+                mod.bias[mod.d_real:] = 0
+
+    @torch.no_grad()
+    def load_unpadded(self, state: dict):
+        """Load the state of the same model held at width d (pad_width=False):
+        each tensor into its leading block, the layer norms' weights times
+        sqrt(d / d_store), then sync_pads()."""
+        own = self.state_dict()
+        if set(own) != set(state):
+            raise ValueError("state of a different model")
+        for name, t in own.items():
+            src = state[name]
+            if src.dim() != t.dim() or any(a > b for a, b in zip(src.shape, t.shape)):
+                raise ValueError(f"{name}: {tuple(src.shape)} does not fit {tuple(t.shape)}")
+            t.zero_()
+            t[tuple(slice(0, n) for n in src.shape)] = src
+        for mod in self.modules():
+            if isinstance(mod, _PLayerNorm):
+                mod.weight[:mod.d_real] *= mod.gain
+        self.sync_pads()
 
     def encode(self, lr):
         """[B, 3, H, W] -> features [B, Hp, Wp, C] padded (reflect) to whole windows."""

@@ -3,7 +3,8 @@ Sec. 3.2). Host-side index logic on the CPU: the decoder's token grid maps to
 the render's Gaussian order with the oracle's reference positions (m points
 per LR pixel at equal intervals, Sec. 3.2), window partition and cyclic shift
 invert, the relative position indices depend on the offset alone, and the
-padded attention heads compute what unpadded ones do. On the GPU: the
+padded attention heads and the padded embedding width compute what unpadded
+ones do. On the GPU: the
 decoder's raw head outputs, rendered by the library with the fused head and
 Algorithm 1's ratio window, match the FP64 oracle on the same rounded values.
 """
@@ -109,6 +110,38 @@ def test_tiny_pipeline_cpu_shapes():
     assert torch.isfinite(raw).all() and torch.equal(raw, raw2)
     with pytest.raises(ValueError):
         GSASR(GSASRConfig(m=12))
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-12), (torch.float32, 2e-5)])
+def test_padded_width_equals_unpadded(dtype, tol):
+    """d = 20 held at 24: the extra channels of the residual stream carry the
+    mean of the real ones, so the width-24 layer norms (eps and weights scaled)
+    equal the width-20 ones; every other extra channel is ignored. The padded
+    model, loaded from the unpadded one, computes the same raw outputs."""
+    from paper_2501_06838_gb300.gsasr import GSASR, GSASRConfig
+    cfg = dict(TINY, d=20, heads=2, head_pad=16)
+    torch.manual_seed(4)
+    a = GSASR(GSASRConfig(**cfg, pad_width=False)).to(dtype)
+    b = GSASR(GSASRConfig(**cfg, pad_width=True)).to(dtype)
+    assert a.cfg.d_store == 20 and b.cfg.d_store == 24
+    with torch.no_grad():    # random, non-trivial layer-norm weights and biases
+        for mod in a.modules():
+            if isinstance(mod, torch.nn.LayerNorm):
+                mod.weight.uniform_(0.5, 1.5)
+                mod.bias.uniform_(-0.3, 0.3)
+    b.load_unpadded(a.state_dict())
+    lr = torch.rand(2, 3, 6, 10, dtype=dtype)
+    sc = torch.tensor([2.0, 3.5])
+    with torch.no_grad():
+        ra, rb = a(lr, sc), b(lr, sc)
+        # the residual stream's extra channels hold the real channels' mean
+        x = b.inject(b.e_base, b.encode(lr), 2, 32, 48)
+    assert ra.shape == rb.shape
+    assert float((ra - rb).abs().max() / ra.abs().max()) < tol
+    assert torch.allclose(x[..., 20:], x[..., :20].mean(-1, keepdim=True).expand(-1, -1, -1, 4),
+                          atol=tol * float(x.abs().max()) * 10)
+    with pytest.raises(ValueError):
+        b.load_unpadded({k: v for k, v in list(a.state_dict().items())[1:]})
 
 
 @pytest.mark.gpu
