@@ -84,6 +84,37 @@ class Gaussians:
         return Gaussians(*ts, ref_grid_m=ref_grid_m)
 
 
+def _need(t: torch.Tensor, shape, dtype, device: torch.device, what: str) -> torch.Tensor:
+    """Host-side check of a caller-supplied buffer before its pointer reaches
+    the library: the library trusts every pointer and size it is given."""
+    if t.device != device:
+        raise ValueError(f"{what} is on {t.device}, the parameters on {device}")
+    if t.dtype != dtype:
+        raise TypeError(f"{what} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous() or tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{what} must be contiguous with shape {tuple(shape)}, "
+                         f"got {tuple(t.shape)}")
+    return t
+
+
+def _device(gs: Sequence[Gaussians], stream=None) -> torch.device:
+    """The one CUDA device all images' parameters are on. It must be the
+    current device, whose stream the library launches on (or the device of
+    the stream passed)."""
+    dev = gs[0].rho.device
+    if dev.type != "cuda":
+        raise ValueError("parameter tensors must be CUDA tensors")
+    for g in gs:
+        for t in g.tensors():
+            if t.device != dev:
+                raise ValueError(f"all parameter tensors must be on one device ({dev}, {t.device})")
+    sdev = stream.device if stream is not None else torch.device("cuda", torch.cuda.current_device())
+    if sdev != dev:
+        raise ValueError(f"parameters are on {dev} but the launch stream is on {sdev}; "
+                         f"use torch.cuda.device({dev}) or pass a stream of that device")
+    return dev
+
+
 def _struct_g(g: Gaussians) -> _abi.GsGaussians:
     ts = g.tensors()
     dt = ts[0].dtype
@@ -96,6 +127,8 @@ def _struct_g(g: Gaussians) -> _abi.GsGaussians:
             raise TypeError("all parameter tensors must share one dtype")
         if not t.is_cuda:
             raise ValueError("parameter tensors must be CUDA tensors")
+        if t.device != ts[0].device:
+            raise ValueError("all parameter tensors must be on one device")
         if not t.is_contiguous() or tuple(t.shape) != shp:
             raise ValueError(f"parameter tensor must be contiguous with shape {shp}, got {tuple(t.shape)}")
     hp = None
@@ -141,6 +174,7 @@ class Workspace:
 
     def __init__(self, nbytes: int, device=None):
         self.buf = torch.empty(int(nbytes), dtype=torch.uint8, device=device or "cuda")
+        self.device = self.buf.device
         if self.buf.data_ptr() % 256:
             raise RuntimeError("workspace allocation is not 256-byte aligned")
 
@@ -161,10 +195,15 @@ def workspace_bytes(gs, views, capacity: int, tile=0, batch=0) -> int:
     return int(b)
 
 
+def _check_ws(ws: Workspace, dev: torch.device):
+    if ws.device != dev:
+        raise ValueError(f"workspace is on {ws.device}, the parameters on {dev}")
+
+
 def count_pairs(gs, views, tile=0, batch=0, stream=None) -> int:
     """Exact number of (tile, Gaussian) pairs; synchronises the stream."""
     n, G, V = _arrays(gs, views, tile, batch)
-    dev = gs[0].rho.device
+    dev = _device(gs, stream)
     ws = Workspace(workspace_bytes(gs, views, 0, tile, batch), dev)
     out = ctypes.c_int64(0)
     _abi.check(_abi.load().gs_count_pairs(n, G, V, ws.ptr, ws.nbytes, _stream(stream),
@@ -184,14 +223,16 @@ def render_batched(gs, views, outs=None, ws: Workspace | None = None, tile=0, ba
                    stream=None, check: bool = False):
     """Forward render of several images in one launch chain. Returns (outs, ws)."""
     n, G, V = _arrays(gs, views, tile, batch)
-    dev = gs[0].rho.device
+    dev = _device(gs, stream)
     if outs is None:
         outs = [torch.empty((3, v.out_h, v.out_w), dtype=torch.float32, device=dev) for v in views]
+    if len(outs) != n:
+        raise ValueError("need one output per image")
     for o, v in zip(outs, views):
-        if o.dtype != torch.float32 or not o.is_contiguous() or tuple(o.shape) != (3, v.out_h, v.out_w):
-            raise ValueError("outputs must be contiguous float32 [3, out_h, out_w]")
+        _need(o, (3, v.out_h, v.out_w), torch.float32, dev, "output")
     if ws is None:
         ws = make_workspace(gs, views, None, tile, batch, stream=stream)
+    _check_ws(ws, dev)
     P = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
     _abi.check(_abi.load().gs_render_batched(n, G, V, P, ws.ptr, ws.nbytes, _stream(stream)),
                "gs_render_batched")
@@ -204,13 +245,19 @@ def render_batched_bwd(gs, views, grad_outs, ws: Workspace, grads=None, tile=0, 
                        stream=None, check: bool = False):
     """Adjoint of the last render_batched on ws. Returns a list of [N_i, 9] float32."""
     n, G, V = _arrays(gs, views, tile, batch)
-    dev = gs[0].rho.device
+    dev = _device(gs, stream)
+    _check_ws(ws, dev)
+    if len(grad_outs) != n:
+        raise ValueError("need one upstream gradient per image")
     grad_outs = [g.contiguous().float() for g in grad_outs]
     for go, v in zip(grad_outs, views):
-        if tuple(go.shape) != (3, v.out_h, v.out_w):
-            raise ValueError("grad_out must be [3, out_h, out_w]")
+        _need(go, (3, v.out_h, v.out_w), torch.float32, dev, "grad_out")
     if grads is None:
         grads = [torch.empty((g.n, 9), dtype=torch.float32, device=dev) for g in gs]
+    if len(grads) != n:
+        raise ValueError("need one gradient buffer per image")
+    for gr, g in zip(grads, gs):
+        _need(gr, (g.n, 9), torch.float32, dev, "gradient buffer")
     GO = (ctypes.c_void_p * n)(*[g.data_ptr() for g in grad_outs])
     GR = (ctypes.c_void_p * n)(*[g.data_ptr() for g in grads])
     _abi.check(_abi.load().gs_render_batched_bwd(n, G, V, GO, GR, ws.ptr, ws.nbytes,
@@ -236,6 +283,9 @@ def render_single_fwd(g: Gaussians, view, out, ws: Workspace, tile=0, batch=0, s
     """Forward through the single-image entry point gs_render_fwd."""
     G = _struct_g(g)
     V = _struct_v(view, tile, batch)
+    dev = _device([g], stream)
+    _check_ws(ws, dev)
+    _need(out, (3, view.out_h, view.out_w), torch.float32, dev, "output")
     _abi.check(_abi.load().gs_render_fwd(ctypes.byref(G), ctypes.byref(V), out.data_ptr(),
                                          ws.ptr, ws.nbytes, _stream(stream)), "gs_render_fwd")
     return out
@@ -246,6 +296,10 @@ def render_single_bwd(g: Gaussians, view, grad_out, grads, ws: Workspace, tile=0
     """Adjoint through the single-image entry point gs_render_bwd."""
     G = _struct_g(g)
     V = _struct_v(view, tile, batch)
+    dev = _device([g], stream)
+    _check_ws(ws, dev)
+    _need(grad_out, (3, view.out_h, view.out_w), torch.float32, dev, "grad_out")
+    _need(grads, (g.n, 9), torch.float32, dev, "gradient buffer")
     _abi.check(_abi.load().gs_render_bwd(ctypes.byref(G), ctypes.byref(V), grad_out.data_ptr(),
                                          grads.data_ptr(), ws.ptr, ws.nbytes, _stream(stream)),
                "gs_render_bwd")
@@ -334,10 +388,14 @@ class Plan:
         ([3, out_h, out_w] float32 per image; [N_i, 9] float32 per image)."""
         self.gs, self.views = list(gs), list(views)
         self.n, self.G, self.V = _arrays(self.gs, self.views, tile, batch)
-        dev = self.gs[0].rho.device
+        dev = _device(self.gs, stream)
         self.ws = make_workspace(self.gs, self.views, capacity, tile, batch, slack, stream)
         self.outs = list(outs) if outs is not None else \
             [torch.empty((3, v.out_h, v.out_w), dtype=torch.float32, device=dev) for v in self.views]
+        if len(self.outs) != self.n:
+            raise ValueError("need one output per image")
+        for o, v in zip(self.outs, self.views):
+            _need(o, (3, v.out_h, v.out_w), torch.float32, dev, "output")
         self.P_out = (ctypes.c_void_p * self.n)(*[o.data_ptr() for o in self.outs])
         self.lib = _abi.load()
         if with_grads:
@@ -345,6 +403,11 @@ class Plan:
                 [torch.zeros_like(o) for o in self.outs]
             self.grads = list(grads) if grads is not None else \
                 [torch.empty((g.n, 9), dtype=torch.float32, device=dev) for g in self.gs]
+            if len(self.grad_outs) != self.n or len(self.grads) != self.n:
+                raise ValueError("need one upstream gradient and one gradient buffer per image")
+            for go, gr, v, g in zip(self.grad_outs, self.grads, self.views, self.gs):
+                _need(go, (3, v.out_h, v.out_w), torch.float32, dev, "grad_out")
+                _need(gr, (g.n, 9), torch.float32, dev, "gradient buffer")
             self.P_go = (ctypes.c_void_p * self.n)(*[g.data_ptr() for g in self.grad_outs])
             self.P_gr = (ctypes.c_void_p * self.n)(*[g.data_ptr() for g in self.grads])
 
@@ -378,6 +441,8 @@ def timing_enable(kernel_names=None):
         ids = {lib.gs_kernel_name(i).decode(): i for i in range(32) if lib.gs_kernel_name(i)}
         mask = 0
         for k in kernel_names:
+            if k not in ids:
+                raise ValueError(f"unknown kernel {k!r}; known: {sorted(ids)}")
             mask |= 1 << ids[k]
     _abi.check(lib.gs_timing_enable(mask), "gs_timing_enable")
 
