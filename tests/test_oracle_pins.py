@@ -344,6 +344,40 @@ def test_adjoint_vs_torch_autograd():
     np.testing.assert_allclose(oracle.render(g, v), I.detach().numpy(), rtol=1e-10, atol=1e-14)
 
 
+@pytest.mark.parametrize("window,norm,head", [(S.WINDOW_SIGMA, S.NORM_DENSITY, False),
+                                               (S.WINDOW_RATIO, S.NORM_PEAK, False),
+                                               (S.WINDOW_SIGMA, S.NORM_DENSITY, True)])
+def test_adjoint_dot_product(window, norm, head):
+    """<g, J d> = <J^T g, d> for the whole render: J d is the directional
+    derivative of the render itself (all Gaussians moved at once along a random
+    direction d, windows frozen) by Richardson-extrapolated central differences;
+    J^T g is the hand adjoint. Ties the adjoint to the forward the parity tests
+    use, not to a per-Gaussian loss routine."""
+    rng = np.random.default_rng(29)
+    h, w, m, s = 6, 5, 4, 2.7
+    g = S.draw_raw_head(3, h, w, m) if head else S.draw_gaussians(3, h, w, m, (0.4, 1.6))
+    v = S.View(h, w, S.out_size(h, s), S.out_size(w, s), s,
+               trunc_k=0.3 if window == S.WINDOW_RATIO else 3.0, norm=norm, window=window)
+    rect = oracle.rects(g, v)
+    go = rng.standard_normal((3, v.out_h, v.out_w))
+    d = [rng.standard_normal(a.shape) for a in g.fields()]
+
+    def loss(t):
+        moved = S.GaussianSet(*(a + t * da for a, da in zip(g.fields(), d)), lr_h=h, lr_w=w,
+                              ref_grid_m=m, head=g.head)
+        return float(np.sum(go * oracle.render(moved, v, frozen_rects=rect, threads=1)))
+
+    # steps of 3e-5: the h^4 remainder and the rounding both stay near 1e-11
+    e = 3e-5
+    c1 = (loss(e) - loss(-e)) / (2 * e)
+    c2 = (loss(2 * e) - loss(-2 * e)) / (4 * e)
+    jd = (4 * c1 - c2) / 3
+    A = oracle.adjoint(g, v, go, threads=1, frozen_rects=rect)
+    flat = np.concatenate([d[0], d[1], d[2][:, None], d[3], d[4][:, None]], 1)
+    jtg = float(np.sum(A * flat))
+    assert abs(jd - jtg) <= 1e-9 * abs(jtg)
+
+
 def test_adjoint_vs_central_difference_config2():
     """Config 2's check: central differences (h = 1e-4) on 64 Gaussians (seed 2)."""
     gs, vs = S.config2()
