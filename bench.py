@@ -859,17 +859,17 @@ def oracle_step(gsets, views, with_adj, band=None, threads=0, grad_outs=None):
     return outs, grads, px
 
 
-def sample_band(gsets, views, with_adj, budget):
-    """None if one oracle step of the whole workload fits in `budget` seconds,
-    else the number of top rows per image that does (probed on 32 rows)."""
+def sample_band(gsets, views, with_adj, seconds):
+    """None if one oracle step of the whole workload fits in `seconds`, else
+    the number of top rows per image that does (probed on 32 rows)."""
     probe = min(32, max(v.out_h for v in views))
     t0 = time.time()
     oracle_step(gsets, views, with_adj, band=probe)
     t = time.time() - t0
     full = t * max(v.out_h for v in views) / probe
-    if full <= budget:
+    if full <= seconds:
         return None
-    return max(16, int(probe * budget / max(t, 1e-9)))
+    return max(16, int(probe * seconds / max(t, 1e-9)))
 
 
 def run_cpu_baseline(gsets, views, with_adj, plan, seconds):
@@ -896,7 +896,7 @@ def run_cpu_baseline(gsets, views, with_adj, plan, seconds):
     cb = {"value": round(px / t / 1e6, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
           "sample": sample + (" (fwd + adjoint)" if with_adj else " (fwd)"),
           "seconds": round(t, 2)}
-    # the same oracle on one core, on a sample of about a tenth of the budget
+    # the same oracle on one core, on a sample of about a tenth of that time
     band1 = sample_band(gsets, views, with_adj, seconds / 10 / max(cores, 1))
     t1 = time.time()
     _, _, px1 = oracle_step(gsets, views, with_adj, band=band1, threads=1)

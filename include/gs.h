@@ -61,7 +61,7 @@ typedef enum {
   GS_ERR_INVALID = 1,      /* bad argument, or (device) a non-finite / out-of-range parameter */
   GS_ERR_CAPACITY = 2,     /* (device) more (tile, Gaussian) pairs than the workspace holds */
   GS_ERR_CUDA = 3,         /* a CUDA runtime call or launch failed */
-  GS_ERR_UNSUPPORTED = 4,  /* a valid request this build does not implement */
+  GS_ERR_UNSUPPORTED = 4,  /* a valid request the library does not implement */
   GS_ERR_TIMEOUT = 5,      /* reserved: a bounded device-side wait gave up */
   GS_ERR_INTERNAL = 6      /* an internal consistency check failed */
 } gs_status;
