@@ -579,3 +579,15 @@ def test_head_adjoint_vs_complex_step_and_fd(head):
     np.testing.assert_allclose(adj, cs, rtol=1e-10, atol=1e-12 * np.abs(cs).max())
     fd = oracle.central_difference(g, v, go, ids[:8], h=1e-5)
     np.testing.assert_allclose(adj[:8], fd, rtol=1e-6, atol=1e-7 * np.abs(fd).max())
+
+
+def test_thread_count_invariance():
+    """The oracle's host threads split the work without changing a bit of the
+    result (no race and a fixed summation order), forward and adjoint."""
+    gs, vs = S.config1()
+    g, v = gs[0], vs[0]
+    go = S.grad_out(1, v.out_h, v.out_w)
+    ref, ref_a = oracle.render(g, v, threads=1), oracle.adjoint(g, v, go, threads=1)
+    for t in (2, 5, 8):
+        assert np.array_equal(oracle.render(g, v, threads=t), ref)
+        assert np.array_equal(oracle.adjoint(g, v, go, threads=t), ref_a)
