@@ -1,7 +1,9 @@
 """Host-side logic of the benchmark (no GPU): the workload views and their
 command-line overrides, the CPU baseline's band sample (it must render with
 the workload's own window and alignment), the algorithmic byte counts behind
-the memory-bound passes' rates, and the whole-pipeline FLOP count."""
+the memory-bound passes' rates, the whole-pipeline FLOP count, and the
+reference arm (the oracle timed on the host cores): its JSON line, alone and
+under a two-rank launch."""
 import argparse
 
 import numpy as np
@@ -84,3 +86,54 @@ def test_pipeline_flops_scale_with_lr_area():
     # padding to whole windows: 90 -> 96 LR px
     f8 = bench.pipeline_flops(cfg, 90, 90)
     assert f8["decoder"] == pytest.approx(bench.pipeline_flops(cfg, 96, 96)["decoder"], rel=1e-12)
+
+
+def _ref_line(out: str) -> dict:
+    import json
+    lines = [l for l in out.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, out
+    return json.loads(lines[0])
+
+
+def test_reference_arm_contract():
+    """bench.py --impl reference times the FP64 oracle on the host cores and
+    prints one JSON line with the contract's keys (no GPU needed)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
+                        "--warmup", "3", "--ref-step-seconds", "0.3"], cwd=root,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = _ref_line(r.stdout)
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 1 and d["warmup"] == 3
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
+    e = d["e2e"]
+    assert (e["value"], e["unit"], e["h2d_bytes_per_step"], e["d2h_bytes_per_step"]) == \
+        (d["value"], d["unit"], 0, 0)
+    assert d["config"]["workload"].startswith("c2")
+
+
+def test_reference_arm_rank0_only():
+    """Under torchrun with two ranks only rank 0 works and prints; both exit 0."""
+    import os
+    import socket
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+                        "--nproc-per-node", "2", "--master-addr", "127.0.0.1", "--master-port",
+                        str(port), "bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1",
+                        "--warmup", "3", "--ref-step-seconds", "0.3"], cwd=root,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = _ref_line(r.stdout)
+    assert d["impl"] == "reference" and d["n_gpus"] == 2
