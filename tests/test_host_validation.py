@@ -145,3 +145,27 @@ def test_half_pixel_scale_limit(lib):
     assert b"2^23" in lib.gs_last_error()
     V[0].scale = 2.0 ** 22
     assert lib.gs_workspace_size(1, G, V, 0) > 0
+
+
+def test_output_bound_matches_out_size(lib):
+    """The library's output bound floor(s * lr) + 1 (s as float32, the product
+    exact in double) agrees with the binding's and the generators' out_size for
+    drawn scales and sizes: out_size + 1 is accepted, out_size + 2 is not."""
+    import importlib
+
+    import numpy as np
+
+    import gs_synthetic as S
+    R = importlib.import_module("paper_2501_06838_gb300.render")
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        lr_h, lr_w = int(rng.integers(1, 400)), int(rng.integers(1, 400))
+        s = float(np.float32(rng.uniform(0.05, 30.0)))
+        oh, ow = R.out_size(lr_h, s), R.out_size(lr_w, s)
+        assert (oh, ow) == (S.out_size(lr_h, s), S.out_size(lr_w, s))
+        G, V = _request()
+        G[0].n, V[0].lr_h, V[0].lr_w, V[0].scale = lr_h * lr_w, lr_h, lr_w, s
+        V[0].out_h, V[0].out_w = oh + 1, ow + 1
+        assert lib.gs_workspace_size(1, G, V, 0) > 0, (lr_h, lr_w, s)
+        V[0].out_h = oh + 2
+        assert lib.gs_workspace_size(1, G, V, 0) == 0, (lr_h, lr_w, s)
