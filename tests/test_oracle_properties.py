@@ -4,8 +4,10 @@ grid and scale (including s < 1), the rectangle loop equals the all-pairs
 brute force that tests the window inequalities pixel by pixel; the hand
 adjoint equals the complex-step derivative of the same forward; the render
 is linear in colour and opacity and additive over disjoint sets of Gaussians;
-and the adjoint is linear in the upstream gradient (the property the row-band
-split of one image relies on)."""
+the adjoint is linear in the upstream gradient (the property the row-band
+split of one image relies on); and with the fused head (drawn head constants,
+raw outputs in) the rectangle loop still equals the brute force and the raw
+adjoint the complex step through the activations."""
 import numpy as np
 import pytest
 
@@ -99,3 +101,43 @@ def test_adjoint_linear_in_upstream_gradient(p):
     a = oracle.adjoint(g, v, g1 + 2.0 * g2, threads=1)
     b = oracle.adjoint(g, v, g1, threads=1) + 2.0 * oracle.adjoint(g, v, g2, threads=1)
     assert _rel(a, b) < 1e-12
+
+
+@st.composite
+def head_problems(draw):
+    m = draw(st.sampled_from([1, 4]))
+    lr_h, lr_w = draw(st.integers(2, 5)), draw(st.integers(2, 5))
+    scale = float(np.float32(draw(st.floats(0.8, 4.0))))
+    head = S.Head(sigma_lo=float(np.float32(draw(st.floats(0.0, 0.5)))),
+                  sigma_span=float(np.float32(draw(st.floats(0.3, 3.0)))),
+                  rho_scale=float(np.float32(draw(st.floats(0.0, 0.95)))),
+                  offset_scale=float(np.float32(draw(st.floats(0.1, 1.0)))),
+                  offset_tanh=draw(st.sampled_from([0, 1])))
+    g = S.draw_raw_head(draw(st.integers(0, 2 ** 31 - 1)), lr_h, lr_w, m, head,
+                        spread=draw(st.sampled_from([0.5, 1.5, 3.0])))
+    window = draw(st.sampled_from([S.WINDOW_SIGMA, S.WINDOW_RATIO]))
+    k = 3.0 if window == S.WINDOW_SIGMA else draw(st.sampled_from([0.15, 0.4]))
+    v = S.View(lr_h, lr_w, max(1, S.out_size(lr_h, scale)), max(1, S.out_size(lr_w, scale)),
+               scale, trunc_k=k, window=window,
+               align=draw(st.sampled_from([S.ALIGN_EQ4, S.ALIGN_HALF])),
+               norm=draw(st.sampled_from([S.NORM_DENSITY, S.NORM_PEAK])))
+    return g, v, np.random.default_rng(draw(st.integers(0, 1000)))
+
+
+@settings(max_examples=25, deadline=None)
+@given(head_problems())
+def test_head_rect_loop_and_adjoint(p):
+    """With the fused head (raw outputs in, drawn head constants): the rectangle
+    loop equals the brute force, and the adjoint with respect to the raw values
+    equals the complex-step derivative through the activations."""
+    g, v, rng = p
+    a = oracle.render(g, v, mode="rect", threads=1)
+    b = oracle.render(g, v, mode="allpairs", threads=1)
+    assert _rel(a, b) < 1e-13
+    go = rng.normal(size=(3, v.out_h, v.out_w))
+    ids = np.arange(min(g.n, 5))
+    adj = oracle.adjoint(g, v, go, threads=1)[ids]
+    cs = oracle.complex_step(g, v, go, ids)
+    for f in range(9):
+        den = max(np.abs(cs[:, f]).max(), 1e-12)
+        assert np.abs(adj[:, f] - cs[:, f]).max() / den < 1e-9, f
