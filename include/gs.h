@@ -217,15 +217,30 @@ gs_status gs_render_fwd(const gs_gaussians* g, const gs_view* v, float* out, voi
 gs_status gs_render_bwd(const gs_gaussians* g, const gs_view* v, const float* grad_out,
                         float* grads, void* ws, size_t ws_bytes, void* stream);
 
-/* The forward of n_images independent images (own Gaussians, sizes and scale
- * each; g, v and outs are host arrays of n_images entries) in one chain of
- * launches over a global tile index space: one kernel per stage, whatever the
- * number of images. */
+/* The forward render (Eq. 4 with the Algorithm-1 window) of n_images
+ * independent images, each with its own Gaussians, LR size, output size, scale
+ * factor and view options (GSASR's training draws the scale factor at random
+ * from [1, 4], Sec. 4.1; a batch may mix scales and sizes),
+ * in one chain of launches over a global tile index space: one kernel per
+ * stage, whatever the number of images.
+ *   g, v, outs: host arrays of n_images entries, read during the call; outs[i]
+ *     is device float32 [3][v[i].out_h][v[i].out_w], fully overwritten.
+ *   All views must agree on tile, batch, binning and adjoint.
+ *   ws: as for gs_render_fwd, sized by gs_workspace_size(n_images, g, v, cap);
+ *     it keeps the state gs_render_batched_bwd needs.
+ * Errors: invalid arguments return GS_ERR_INVALID before any launch (message
+ * in gs_last_error); invalid parameter values and pair-capacity overflow are
+ * flagged in the workspace status word (gs_sync_status). Capture-safe: no
+ * host synchronisation, no allocation. */
 gs_status gs_render_batched(int32_t n_images, const gs_gaussians* g, const gs_view* v,
                             float* const* outs, void* ws, size_t ws_bytes, void* stream);
 
-/* Adjoint of the last gs_render_batched on `ws`. grad_outs, grads: host arrays
- * of device pointers as in gs_render_bwd, one per image. */
+/* Adjoint of the last gs_render_batched on `ws` (same g and v, unchanged
+ * values), windows held fixed as in gs_render_bwd. grad_outs, grads: host
+ * arrays of n_images device pointers; grad_outs[i] is float32
+ * [3][out_h][out_w] (dL/dI of image i), grads[i] is float32 [n_i][9] in the
+ * order of gs_render_bwd, overwritten. Errors as for gs_render_batched.
+ * Capture-safe. */
 gs_status gs_render_batched_bwd(int32_t n_images, const gs_gaussians* g, const gs_view* v,
                                 const float* const* grad_outs, float* const* grads, void* ws,
                                 size_t ws_bytes, void* stream);
@@ -282,6 +297,8 @@ int64_t gs_launch_count(void);
 gs_status gs_timing_enable(int32_t kernel_mask);
 int32_t gs_timing_read(double* ms_out, int64_t* count_out, int32_t n);
 gs_status gs_timing_release(void);
+/* Static name of kernel id `id` ("raster_fwd", "raster_bwd", ...); "" for an
+ * id out of range. */
 const char* gs_kernel_name(int32_t id);
 
 /* Measured throughputs of the units that bound the raster kernels. */
