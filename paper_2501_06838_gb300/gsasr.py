@@ -30,6 +30,14 @@ are random, so only the timing means anything. The network runs in PyTorch
 (cuBLAS GEMMs and PyTorch's fused attention kernels); only the render is this
 library's own code.
 
+Storage width. The width-d stream is held at d_store = 184 channels (d rounded
+up to a multiple of 8) so that every GEMM has 16-byte aligned BF16 rows. The
+extra channels of the residual stream each carry the mean of the d real ones
+(every layer adding into the stream has its extra output rows set to the mean
+of its real rows), which lets one fused LayerNorm of width d_store compute the
+width-d one exactly (_PLayerNorm); all other extra channels are zero and
+ignored. load_unpadded() maps the state of the width-d model.
+
 Token layout. The decoder keeps its tokens on the sub-pixel grid
 [B, sqrt(m) Hp, sqrt(m) Wp, d]: token (ty, tx) is the Gaussian whose reference
 position is (x, y) = ((tx + 1/2) / sqrt(m) - 1/2, (ty + 1/2) / sqrt(m) - 1/2)
