@@ -68,8 +68,12 @@ def band_rows(out_h: int, parts: int, tile: int = 16) -> list[tuple[int, int]]:
 
 
 def band_view(view, row0: int, rows: int):
-    """A copy of `view` restricted to image rows row0 .. row0 + rows - 1."""
+    """A copy of `view` restricted to image rows row0 .. row0 + rows - 1.
+    rows must be >= 1: a rank whose band from band_rows() is empty renders
+    nothing and passes zero gradients to allreduce_band_grads()."""
     import copy
+    if rows < 1 or row0 < 0:
+        raise ValueError(f"band of {rows} rows at row {row0}: an empty band renders nothing")
     v = copy.copy(view)
     v.out_h = rows
     v.row0 = row0

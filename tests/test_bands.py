@@ -42,6 +42,24 @@ def test_band_rows_partition():
         band_rows(10, 0)
 
 
+def test_band_view():
+    """band_view restricts a view to its rows and keeps every other field; an
+    empty band (more ranks than tile rows) is refused, not sent to the library."""
+    from paper_2501_06838_gb300.render import View
+    from paper_2501_06838_gb300.shard import band_view
+    v = View(48, 40, 192, 160, 4.0, trunc_k=0.1, norm=1, window=1, align=1)
+    b = band_view(v, 64, 32)
+    assert (b.row0, b.out_h) == (64, 32) and (v.row0, v.out_h) == (0, 192)
+    assert (b.lr_h, b.lr_w, b.out_w, b.scale, b.trunc_k, b.norm, b.window, b.align) == \
+        (48, 40, 160, 4.0, 0.1, 1, 1, 1)
+    bands = band_rows(20, 4, 16)        # two tile rows over four ranks: two empty bands
+    assert sum(1 for _, n in bands if n == 0) == 2
+    for r0, n in bands:
+        if n == 0:
+            with pytest.raises(ValueError, match="empty band"):
+                band_view(v, r0, n)
+
+
 def _masked(go, r0, n):
     m = np.zeros_like(go)
     m[:, r0:r0 + n] = go[:, r0:r0 + n]
