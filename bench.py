@@ -290,7 +290,6 @@ def run_gpu(args, rank, world, local_rank):
     import torch.distributed as dist
 
     import paper_2501_06838_gb300 as gs
-    from paper_2501_06838_gb300 import build as libbuild
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)

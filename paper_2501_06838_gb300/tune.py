@@ -11,8 +11,6 @@ from __future__ import annotations
 import ctypes
 import os
 
-import torch
-
 from . import _abi
 from .render import Plan, _stream
 

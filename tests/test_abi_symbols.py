@@ -1,6 +1,5 @@
 """The C-ABI library builds, loads without a GPU and exports every function
 include/gs.h declares; host-only entry points behave (no CUDA call made)."""
-import ctypes
 import os
 import re
 

@@ -3,11 +3,10 @@ arguments are rejected before any launch; invalid parameter values and a pair
 count above the workspace's capacity are flagged by the kernels in the
 workspace status word and reported by gs_sync_status. Nothing here faults,
 traps or waits on the device."""
-import numpy as np
 import pytest
 
 import gs_synthetic as S
-from _util import absolute, device_gaussians
+from _util import device_gaussians
 
 
 def test_missing_library_fails_loudly(tmp_path):

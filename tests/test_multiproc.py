@@ -3,8 +3,6 @@ collective); its host logic is tested with world_size 2 over gloo on CPU."""
 import os
 import socket
 
-import pytest
-
 import gs_synthetic as S
 from paper_2501_06838_gb300.shard import image_costs, shard_images
 

@@ -87,7 +87,6 @@ def test_high_correlation_and_tiny_sigma():
 
 
 def test_empty_and_single_pixel():
-    import torch
     import paper_2501_06838_gb300 as gs
     # no Gaussians at all -> zeros
     e = S.GaussianSet(np.zeros((0, 2)), np.ones((0, 2)), np.zeros(0), np.zeros((0, 3)),

@@ -1,7 +1,6 @@
 """Autotuner (gs_tune): times the launch candidates on the workload, returns
 the fastest, and serves the cached choice on the next call; the choice renders
 the same image."""
-import numpy as np
 import pytest
 
 import gs_synthetic as S
