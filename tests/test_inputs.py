@@ -131,3 +131,20 @@ def test_seeded_and_deterministic():
     y5, k5, t5 = S.config5_batch(3, batch=2)
     assert s5 == t5 and np.array_equal(x5, y5) and all(np.array_equal(p, q) for p, q in zip(h5, k5))
     assert all(h.shape == (3, S.out_size(48, s), S.out_size(48, s)) for h, s in zip(h5, s5))
+
+
+def test_bf16_rounding_matches_torch():
+    """The generators' float32 -> bfloat16 rounding (round to nearest even, on
+    the bit pattern) equals torch's conversion on CPU, ties and subnormals
+    included; float16 storage is numpy's IEEE conversion."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(8)
+    x = np.concatenate([rng.standard_normal(20000) * 10.0 ** rng.integers(-6, 6, 20000),
+                        np.float32(1.0) + np.arange(-64, 64) * np.float32(2.0 ** -16),  # ties
+                        np.array([0.0, -0.0, 1e-40, -3e-39, 3.0e38, -1.7e38])]).astype(np.float32)
+    ours = S.bf16_bits_to_f32(S.round_bf16_bits(x))
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float32).numpy()
+    np.testing.assert_array_equal(ours.view(np.uint32), ref.view(np.uint32))
+    h = x[np.abs(x) < 65504]   # within float16's range
+    np.testing.assert_array_equal(S.storage_round(h.astype(np.float64), "f16"),
+                                  h.astype(np.float16).astype(np.float64))
