@@ -11,8 +11,10 @@ pixel (N = 65,536), x4 -> 1024x1024, forward + adjoint, FP32 parameters.
 
 Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on
 the launching stream; L2 is flushed (256 MiB write) before every step, outside
-the events. Under torchrun every rank renders its own copy of the workload
-(weak scaling, no collective on the data path); rank 0 prints one JSON line.
+the events. Under torchrun the job is split over the ranks (shard_workload):
+images over ranks with no collective, or one image in row bands with an
+all-reduce of the gradients; the time is the max over ranks and rank 0 prints
+one JSON line.
 """
 from __future__ import annotations
 
@@ -201,16 +203,65 @@ def apply_view_flags(views, args):
 # Clock sampling during the timed region
 # --------------------------------------------------------------------------
 class ClockSampler:
+    """SM clock, power and clock-event reasons of one GPU, sampled every 2 ms
+    from a thread through NVML (read-only queries; nvidia-smi at 200 ms if the
+    NVML library cannot be loaded) while the timed region runs."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, interval_s: float = 0.002):
         self.gpu = gpu_index
-        self.samples = []
+        self.interval = interval_s
+        self.samples = []   # (sm_mhz, max_mhz, reason bits or names)
         self.proc = None
+        self.nvml = None
+        self.handle = None
+        self._stop = threading.Event()
+        self.thread = None
+
+    def _open_nvml(self):
+        import ctypes
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+        except OSError:
+            return False
+        if lib.nvmlInit_v2() != 0:
+            return False
+        h = ctypes.c_void_p()
+        ok = False
+        try:
+            import torch
+            p = torch.cuda.get_device_properties(self.gpu)
+            bus = f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0".encode()
+            ok = lib.nvmlDeviceGetHandleByPciBusId_v2(ctypes.c_char_p(bus), ctypes.byref(h)) == 0
+        except Exception:
+            ok = False
+        if not ok and lib.nvmlDeviceGetHandleByIndex_v2(self.gpu, ctypes.byref(h)) != 0:
+            return False
+        self.nvml, self.handle = lib, h
+        return True
+
+    def _nvml_loop(self):
+        import ctypes
+        lib, h = self.nvml, self.handle
+        clk, mx, reasons = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx))
+        get_reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self._stop.is_set():
+            if lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0 and \
+                    get_reasons(h, ctypes.byref(reasons)) == 0:
+                self.samples.append((float(clk.value), float(mx.value), int(reasons.value)))
+            time.sleep(self.interval)
 
     def start(self):
+        if self._open_nvml():
+            self.thread = threading.Thread(target=self._nvml_loop, daemon=True)
+            self.thread.start()
+            return
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
@@ -219,37 +270,47 @@ class ClockSampler:
         except Exception:
             self.proc = None
             return
-        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread = threading.Thread(target=self._smi_loop, daemon=True)
         self.thread.start()
 
-    def _read(self):
+    def _smi_loop(self):
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
         for line in self.proc.stdout:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) >= 9:
-                self.samples.append(parts)
+                try:
+                    sm, mx = float(parts[1]), float(parts[2])
+                except ValueError:
+                    continue
+                self.samples.append((sm, mx, {n for n, v in zip(names, parts[5:9])
+                                              if "Active" in v and "Not" not in v}))
 
     def stop(self):
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        time.sleep(0.25)
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except Exception:
-            self.proc.kill()
-        def num(x):
+        if self.nvml is not None:
+            self._stop.set()
+            self.thread.join(timeout=5)
+            src = f"nvml every {self.interval * 1e3:g} ms"
+        elif self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
             try:
-                return float(x)
-            except ValueError:
-                return None
-        sm = [num(s[1]) for s in self.samples if num(s[1])]
-        mx = [num(s[2]) for s in self.samples if num(s[2])]
-        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        reasons = sorted({n for s in self.samples for n, v in zip(names, s[5:9]) if "Active" in v
-                          and "Not" not in v})
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            src = "nvidia-smi every 200 ms"
+        else:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock sampling unavailable"]}
+        sm = [s[0] for s in self.samples]
+        mx = [s[1] for s in self.samples]
+        reasons = set()
+        for s in self.samples:
+            if isinstance(s[2], set):
+                reasons |= s[2]
+            else:
+                reasons |= {n for b, n in self.REASONS.items() if s[2] & b}
         return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(self.samples)}
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.samples), "source": src}
 
 
 # --------------------------------------------------------------------------
@@ -285,16 +346,74 @@ def hbm_stage_rates(stage_raw, steps, stats, dtname, grid):
     return out
 
 
+# The parameter draws of each single-image workload, so that a rank can render
+# another image of the same shape (seed = its index in the batch; index 0 is
+# the workload's own image).
+SIGMA_RANGE = {"c1": (0.3, 2.0), "c2": (0.3, 2.0), "rab4": (0.2, 3.0), "rab8": (0.2, 3.0)}
+
+
+def batch_member(name, g, index):
+    """Image `index` of a batch of images shaped like `g` (the workload's)."""
+    if index == 0:
+        return g
+    rng = SIGMA_RANGE.get(name, (0.2, 3.0) if name.startswith("c4x") else (0.3, 2.0))
+    return S.draw_gaussians(index, g.lr_h, g.lr_w, g.ref_grid_m, rng, dtype=g.dtype)
+
+
+def shard_workload(args, gsets, views, rank, world):
+    """The part of the job that rank `rank` of `world` renders, and how the
+    job is split (host logic only; no GPU):
+      images: a multi-image workload's images partitioned over the ranks,
+              longest first (shard.shard_images), no collective: a fixed batch
+              (strong scaling); a single-image workload becomes a batch of
+              `world` images of its shape, one per rank (weak scaling);
+      bands:  the rows of a single image split into one band per rank
+              (shard.band_rows / band_view); the forward needs no exchange and
+              the adjoint's per-band gradients are summed over the ranks with
+              one all-reduce of N x 9 floats (strong scaling).
+    Returns (gsets, views, info)."""
+    from paper_2501_06838_gb300 import shard
+    job_pix = sum(v.out_h * v.out_w for v in views)
+    if world == 1:
+        return gsets, views, {"mode": "none", "scaling": "weak", "job_hr_pixels": job_pix,
+                              "parallelism": "one GPU"}
+    mode = args.shard
+    if mode == "bands":
+        if len(views) != 1:
+            raise SystemExit("--shard bands splits one image: use it with a single-image workload")
+        tile = args.tile or 16
+        r0, rows = shard.band_rows(views[0].out_h, world, tile)[rank]
+        if rows < 1:
+            raise SystemExit(f"{views[0].out_h} rows give rank {rank} an empty band")
+        return gsets, [shard.band_view(views[0], r0, rows)], {
+            "mode": "bands", "scaling": "strong", "job_hr_pixels": job_pix, "band": [r0, rows],
+            "parallelism": f"row bands of one image over {world} ranks (rows {r0}..{r0 + rows - 1} "
+                           f"on rank {rank}), all-reduce of the N x 9 gradients"}
+    if len(views) > 1:
+        parts = shard.shard_images(shard.image_costs(views), world)
+        mine = parts[rank]
+        return [gsets[i] for i in mine], [views[i] for i in mine], {
+            "mode": "images", "scaling": "strong", "job_hr_pixels": job_pix, "rank_images": mine,
+            "parallelism": f"{len(views)} images partitioned over {world} ranks (longest first, "
+                           f"images {mine} on rank {rank}), no collective"}
+    return [batch_member(args.workload, gsets[0], rank)], views, {
+        "mode": "images", "scaling": "weak", "job_hr_pixels": world * job_pix,
+        "parallelism": f"a batch of {world} images of this shape, one per rank, no collective"}
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
 
     import paper_2501_06838_gb300 as gs
+    from paper_2501_06838_gb300 import shard
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     gsets, views, with_adj, dtname = workload(args.workload, args)
     views = apply_view_flags(views, args)
+    gsets, views, shard_info = shard_workload(args, gsets, views, rank, world)
+    band_allreduce = shard_info["mode"] == "bands" and with_adj
     tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[dtname]
 
     def dev_g(g):
@@ -328,6 +447,8 @@ def run_gpu(args, rank, world, local_rank):
         plan.fwd(stream)
         if with_adj:
             plan.bwd(stream)
+            if band_allreduce:
+                shard.allreduce_band_grads(plan.grads[0])
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -399,6 +520,8 @@ def run_gpu(args, rank, world, local_rank):
             plan.fwd(stream)
             if with_adj:
                 plan.bwd(stream)
+                if band_allreduce:
+                    shard.allreduce_band_grads(plan.grads[0])
             ev[k][1].record(stream)
         torch.cuda.synchronize()
         launches = gs.launch_count() - launches0
@@ -407,7 +530,17 @@ def run_gpu(args, rank, world, local_rank):
     timed_ktimes = dict(ktimes)
     if world > 1:
         dist.barrier()
+    # a clock-sampled repeat of the same steps right after the timed region,
+    # so that a short timed region still gets enough clock samples under load
+    n_timed_samples = len(clocks.samples)
+    t_rep = time.time()
+    while len(clocks.samples) < n_timed_samples + 25 and time.time() - t_rep < 2.0:
+        for _ in range(args.steps):
+            flush.zero_()
+            step()
+        torch.cuda.synchronize()
     clk = clocks.stop()
+    clk["samples_timed_region"] = n_timed_samples
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
 
@@ -484,10 +617,12 @@ def run_gpu(args, rank, world, local_rank):
                 "pairs_per_launch": pairs, "ms_per_launch": round(ms / cnt, 5)}
 
     res = {
-        "metric": METRIC, "value": round(world * hr_pix * args.steps / (total_ms * 1e-3) / 1e6, 2),
+        "metric": METRIC,
+        "value": round(shard_info["job_hr_pixels"] * args.steps / (total_ms * 1e-3) / 1e6, 2),
         "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(total_ms / args.steps, 5), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": dtname, "data": "synthetic",
+        "scaling": shard_info["scaling"], "vs_baseline": None, "dtype": dtname,
+        "data": "synthetic",
         "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}",
                    "view": view_desc(views[0]),
                    "l2": "flushed before every step (256 MiB write, outside the timed events)",
@@ -498,8 +633,9 @@ def run_gpu(args, rank, world, local_rank):
                                                             "from_cache", "n_timed")},
                    "adjoint": "gaussian-warp" if plan.V[0].adjoint == 2 else "tile",
                    "cuda_graph": bool(use_graph),
-                   "hr_pixels_per_step": hr_pix, "gaussians": sum(g.n for g in dgs),
-                   "parallelism": f"replicas x{world} (one full workload per GPU)"},
+                   "hr_pixels_per_step": shard_info["job_hr_pixels"],
+                   "gaussians": sum(g.n for g in dgs),
+                   "parallelism": shard_info["parallelism"]},
         "fwd_mpix_s": round(hr_pix * args.steps / (sum(fwd_ms) * 1e-3) / 1e6, 2),
         "kernel_ms": {k: round(v[0] / v[1], 5) for k, v in ktimes.items()},
         "kernel_ms_note": (f"the dominant kernel timed by CUDA events inside the timed region"
@@ -526,14 +662,15 @@ def run_gpu(args, rank, world, local_rank):
             t = torch.tensor([tot], dtype=torch.float64, device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             tot = float(t.item())
-        e2e["value"] = round(world * hr_pix * args.steps / (tot * 1e-3) / 1e6, 2)
+        e2e["value"] = round(shard_info["job_hr_pixels"] * args.steps / (tot * 1e-3) / 1e6, 2)
         e2e["ms_per_step"] = round(tot / args.steps, 5)
         pt = e2e.pop("pipelined_total_ms")
         if world > 1:
             t = torch.tensor([pt], dtype=torch.float64, device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             pt = float(t.item())
-        e2e["pipelined"] = {"value": round(world * hr_pix * args.steps / (pt * 1e-3) / 1e6, 2),
+        e2e["pipelined"] = {"value": round(shard_info["job_hr_pixels"] * args.steps /
+                                          (pt * 1e-3) / 1e6, 2),
                             "ms_per_step": round(pt / args.steps, 5),
                             "l2": "not flushed between the overlapping steps; every step copies "
                                   "all its inputs in and all its results out"}
@@ -546,6 +683,22 @@ def run_gpu(args, rank, world, local_rank):
         if err:
             res["error_vs_oracle"] = err
     return res
+
+
+def run_x12(args, rank, world, local_rank):
+    """The x12 half of the metric beside the default x4 line: config 4 at x12
+    (LR 480x270, m = 4, N = 518,400 -> 5760x3240, BF16 parameters), forward +
+    adjoint, with the same steps and warm-up, its own clock record and
+    roofline."""
+    a = argparse.Namespace(**vars(args))
+    a.workload, a.no_e2e, a.no_cpu, a.no_probe, a.tune, a.graph = \
+        "c4x12-bf16", True, True, True, False, None
+    r = run_gpu(a, rank, world, local_rank)
+    keep = ("value", "unit", "ms_per_step", "steps", "warmup", "dtype", "fwd_mpix_s", "kernel_ms",
+            "stage_ms_per_step", "pairs", "roofline", "clocks", "gpu_launches")
+    out = {"workload": r["config"]["workload"]}
+    out.update({k: r[k] for k in keep if k in r})
+    return out
 
 
 def run_train(args, rank, world, local_rank):
@@ -982,6 +1135,12 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-probe", action="store_true", help="skip the unit-throughput probe")
+    ap.add_argument("--shard", choices=["auto", "images", "bands"], default="auto",
+                    help="with several GPUs: partition images over the ranks (a single image "
+                         "becomes a batch of one image per rank), or split one image into row "
+                         "bands with an all-reduce of the gradients")
+    ap.add_argument("--no-x12", action="store_true",
+                    help="c2 only: skip the x12 measurement (config 4, BF16) added to the line")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--graph", dest="graph", action="store_true", default=None,
                     help="time each step as one CUDA-graph replay (default for c3 / c3eq)")
@@ -1020,6 +1179,8 @@ def main():
         res = run_train(args, rank, world, local_rank)
     else:
         res = run_gpu(args, rank, world, local_rank)
+        if args.workload == "c2" and not args.no_x12:
+            res["x12"] = run_x12(args, rank, world, local_rank)
     if rank == 0:
         print(json.dumps(res), flush=True)
     if world > 1:

@@ -93,8 +93,10 @@ typedef enum { GS_WINDOW_SIGMA = 0, GS_WINDOW_RATIO = 1 } gs_window;
 typedef enum { GS_ALIGN_EQ4 = 0, GS_ALIGN_HALF = 1 } gs_align;
 
 /* How the adjoint sums each Gaussian's record-space moments over its window:
- *   TILE:     one CTA per screen tile, per-tile partial sums reduced across the
- *             warp and added with atomics (summation order varies run to run);
+ *   TILE:     one warp per screen tile, one lane per Gaussian of the tile's
+ *             list (the tile's upstream gradient read from shared memory by
+ *             every lane at once); each (tile, Gaussian) sum is added with
+ *             atomics (summation order varies run to run);
  *   GAUSSIAN: one warp per Gaussian over its own window, one fixed summation
  *             order, no atomics: bitwise deterministic;
  *   AUTO:     the library's choice (currently TILE, the faster of the two on
@@ -163,7 +165,9 @@ typedef struct gs_view {
                            <= 0: whole image */
   int32_t norm;         /* gs_norm */
   int32_t tile;         /* screen tile edge in HR px: 8, 16 or 32 (0 = 16) */
-  int32_t batch;        /* Gaussians per shared-memory batch, 32..512 (0 = default) */
+  int32_t batch;        /* Gaussians staged in shared memory per round of the raster: 0
+                           (default: the smaller), 32 or 64 at tile 8 and 16, 64 or 128 at
+                           tile 32 (one or two per thread); other values are GS_ERR_INVALID */
   int32_t window;       /* gs_window */
   int32_t align;        /* gs_align */
   int32_t adjoint;      /* gs_adjoint; every view of one batched call must agree */
@@ -255,17 +259,27 @@ gs_status gs_render_batched_bwd(int32_t n_images, const gs_gaussians* g, const g
  *     for the per-Gaussian state (about 130 bytes per Gaussian) or for the
  *     (tile, Gaussian) pairs (16 bytes each), are rejected with
  *     GS_ERR_UNSUPPORTED and a message saying how much they need.
- *   - The first call with a given device current looks up the array's device
- *     address (cudaGetSymbolAddress); make that first call before any stream
- *     capture.
+ *   - Every call looks up the array's device address in the current device's
+ *     context (cudaGetSymbolAddress).
  *   - Each call counts the pairs first, synchronising `stream`, then launches
- *     the render asynchronously on `stream`.
+ *     the render asynchronously on `stream`. Because of that synchronisation
+ *     the call can never be made while `stream` is being captured into a
+ *     CUDA graph.
  *   - All calls share the one array and each leaves its state there: calls
  *     that overlap on the GPU (other streams, other host threads) race and
  *     give wrong images. gs_render_bwd cannot follow this call.
+ *   - Problems the kernels find while they run (an internal check, a count
+ *     above the capacity) are left in the array's status word: read them with
+ *     gs_noalloc_sync_status after the call.
  * g, v, out: as for gs_render_fwd (device parameters, device output). */
 gs_status gs_render_fwd_noalloc(const gs_gaussians* g, const gs_view* v, float* out,
                                 void* stream);
+
+/* The device status of the last gs_render_fwd_noalloc, for callers without a
+ * workspace pointer: synchronises `stream`, returns the static scratch's status
+ * word as gs_sync_status does for a workspace, and resets it to GS_OK. Like the
+ * call it follows, it has no counterpart in the paper. */
+gs_status gs_noalloc_sync_status(void* stream);
 
 /* Synchronises `stream`, returns the workspace's device status word and resets
  * it to GS_OK. */

@@ -26,7 +26,7 @@ EXPORTS = ("gs_workspace_size", "gs_count_pairs", "gs_render_fwd", "gs_render_bw
            "gs_render_batched", "gs_render_batched_bwd", "gs_sync_status", "gs_read_stats",
            "gs_last_error", "gs_status_string", "gs_launch_count", "gs_timing_enable",
            "gs_timing_read", "gs_timing_release", "gs_kernel_name", "gs_version",
-           "gs_render_fwd_noalloc", "gs_probe_peaks", "gs_tune")
+           "gs_render_fwd_noalloc", "gs_noalloc_sync_status", "gs_probe_peaks", "gs_tune")
 
 
 class GsHead(ctypes.Structure):
@@ -117,6 +117,7 @@ def load(path: str | None = None):
             "gs_kernel_name": (ctypes.c_char_p, [i32]),
             "gs_version": (ctypes.c_char_p, []),
             "gs_render_fwd_noalloc": (i32, [G, V, vp, vp]),
+            "gs_noalloc_sync_status": (i32, [vp]),
             "gs_probe_peaks": (i32, [vp, sz, vp, ctypes.POINTER(GsPeaks)]),
             "gs_tune": (i32, [i32, G, V, fpp, fpp, fpp, vp, sz, vp, i32, ctypes.c_char_p,
                               ctypes.POINTER(GsTuning)]),

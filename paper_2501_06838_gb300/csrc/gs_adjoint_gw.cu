@@ -4,28 +4,25 @@
 // and written once, with no atomics (deterministic bit for bit).
 //
 // Per Gaussian the warp needs, over its window, with G = sum_k g_k c_k,
-// w = 2^e and the record's X = x - cx, Y = y - cy (HR px):
-//   SX = sum G w X, SY = sum G w Y, SXX = sum G w X^2, SXY = sum G w X Y,
+// w = 2^e and the record's exponent e = -d^2 + g Y^2 + l in the completed
+// square's coordinates d = sA X - sK Y, Y = y - cy (HR px):
+//   Sd = sum G w d, SY = sum G w Y, Sdd = sum G w d^2, SdY = sum G w d Y,
 //   SYY = sum G w Y^2, C_k = sum g_k w,
 // the same eight moments the tile adjoint leaves (k_preprocess_bwd turns them
 // into parameter gradients).
 //
 // Layout of the walk:
 //   - the window's rows go through a per-warp row table in shared memory,
-//     (Y, Y, R, R) with R = g Y^2 + l the row part of the exponent (completed
-//     square: e = -(sA X - sK Y)^2 + R), filled 64 rows at a time;
+//     (Y, Y, R, R) with R = g Y^2 + l the row part of the exponent, filled 64
+//     rows at a time;
 //   - each lane owns a pair of adjacent columns (x, x + 1): the grad_out loads
 //     are float2 (8-byte aligned when the row width is even) and all FP32 work
 //     is packed two-wide (FFMA2 etc.), one instruction for both columns;
 //   - columns go in chunks of up to 32 pairs; a narrow chunk (< 17 pairs)
 //     gives the spare lanes further rows, so a warp covers 32/cw rows of cw
-//     column pairs per step and few lanes idle;
-//   - X is constant for a lane within a chunk, so the X moments follow from
-//     the chunk's per-lane sums: SX += X S0, SXX += X^2 S0, SXY += X SY with
-//     S0 = c . C (Y moments are summed per pixel about the centre, which keeps
-//     them accurate however far the window extends).
-// Masked columns (outside [x0, x1], or lanes past the chunk) take sA X = +inf,
-// so e = -inf and w = +0 with no branch.
+//     column pairs per step and few lanes idle.
+// Masked columns (outside [x0, x1], or lanes past the chunk) take sA X = 1e18,
+// so d stays finite, e = -1e36 and w = +0 with no branch.
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -34,7 +31,7 @@ namespace {
 
 constexpr int kGwWarps = 8;    // Gaussians (warps) per CTA
 constexpr int kGwRows = 64;    // rows per row-table block
-constexpr float kInfGw = __builtin_huge_valf();
+constexpr float kFarGw = 1e18f;   // masked column: w = +0, every moment product 0
 
 __device__ __forceinline__ float2 p2(float a, float b) { return make_float2(a, b); }
 
@@ -64,7 +61,7 @@ __device__ __forceinline__ float warp_sum8(const float (&v)[8], int lane) {
 }
 
 struct GwAcc {
-  float2 C[3], SY, SYY;
+  float2 C[3], SY, SYY, Sd, Sdd, SdY;
 };
 
 // One step: the lane's column pair on table row `q` (Y, Y, R, R), loads at
@@ -91,9 +88,14 @@ __device__ __forceinline__ void gw_pixel_pair(GwAcc& a, const float* __restrict_
   const float2 e = __ffma2_rn(p2(-d.x, -d.y), d, p2(q.z, q.w));  // R - d^2
   const float2 wv = p2(ex2_approx(e.x), ex2_approx(e.y));
   const float2 G = __ffma2_rn(gb, cb, __ffma2_rn(gg, cg, __fmul2_rn(gr, cr)));
-  const float2 GwY = __fmul2_rn(__fmul2_rn(G, wv), Y);
+  const float2 Gw = __fmul2_rn(G, wv);
+  const float2 GwY = __fmul2_rn(Gw, Y);
+  const float2 Gwd = __fmul2_rn(Gw, d);
   a.SY = __fadd2_rn(a.SY, GwY);
   a.SYY = __ffma2_rn(GwY, Y, a.SYY);
+  a.Sd = __fadd2_rn(a.Sd, Gwd);
+  a.Sdd = __ffma2_rn(Gwd, d, a.Sdd);
+  a.SdY = __ffma2_rn(Gwd, Y, a.SdY);
   a.C[0] = __ffma2_rn(gr, wv, a.C[0]);
   a.C[1] = __ffma2_rn(gg, wv, a.C[1]);
   a.C[2] = __ffma2_rn(gb, wv, a.C[2]);
@@ -112,8 +114,8 @@ __device__ __forceinline__ void gw_walk(const float* __restrict__ go, int64_t pl
   const float* g2 = go + 2 * plane;
   const int xs = x0 & ~1;
   const int np = ((x1 - xs) >> 1) + 1;   // column pairs covering [xs, x1]
-  float2 tSX = p2(0.f, 0.f), tSXX = tSX, tSXY = tSX, tSY = tSX, tSYY = tSX;
-  float2 tC0 = tSX, tC1 = tSX, tC2 = tSX;
+  float2 tSd = p2(0.f, 0.f), tSdd = tSd, tSdY = tSd, tSY = tSd, tSYY = tSd;
+  float2 tC0 = tSd, tC1 = tSd, tC2 = tSd;
 
   for (int rb = y0; rb <= y1; rb += kGwRows) {
     const int nr = min(kGwRows, y1 - rb + 1);
@@ -134,11 +136,11 @@ __device__ __forceinline__ void gw_walk(const float* __restrict__ go, int64_t pl
       const float2 X = p2(__fsub_rn(__fsub_rn((float)xp, cxh), cxl),
                           __fsub_rn(__fsub_rn((float)(xp + 1), cxh), cxl));
       float2 Xs = p2(sA * X.x, sA * X.y);
-      if (!live || xp < x0) Xs.x = kInfGw;
-      if (!live || xp + 1 > x1) Xs.y = kInfGw;
+      if (!live || xp < x0) Xs.x = kFarGw;
+      if (!live || xp + 1 > x1) Xs.y = kFarGw;
       const int xq = min(xp + 1, W - 1);
       GwAcc a;
-      a.C[0] = a.C[1] = a.C[2] = a.SY = a.SYY = p2(0.f, 0.f);
+      a.C[0] = a.C[1] = a.C[2] = a.SY = a.SYY = a.Sd = a.Sdd = a.SdY = p2(0.f, 0.f);
       int r = lr;
       for (; r + rpi < nr; r += 2 * rpi) {
         const int64_t ya = (int64_t)(rb + r) * W, yb = ya + (int64_t)rpi * W;
@@ -150,12 +152,9 @@ __device__ __forceinline__ void gw_walk(const float* __restrict__ go, int64_t pl
         const int64_t ya = (int64_t)(rb + r) * W;
         gw_pixel_pair<ALIGNED>(a, g0, g1, g2, ya + xp, ya + xq, rt[r], Xs, nsK, cr, cg, cb);
       }
-      // fold the chunk: X is constant per lane column
-      const float2 S0 = __ffma2_rn(cb, a.C[2], __ffma2_rn(cg, a.C[1], __fmul2_rn(cr, a.C[0])));
-      const float2 XS0 = __fmul2_rn(X, S0);
-      tSX = __fadd2_rn(tSX, XS0);
-      tSXX = __ffma2_rn(X, XS0, tSXX);
-      tSXY = __ffma2_rn(X, a.SY, tSXY);
+      tSd = __fadd2_rn(tSd, a.Sd);
+      tSdd = __fadd2_rn(tSdd, a.Sdd);
+      tSdY = __fadd2_rn(tSdY, a.SdY);
       tSY = __fadd2_rn(tSY, a.SY);
       tSYY = __fadd2_rn(tSYY, a.SYY);
       tC0 = __fadd2_rn(tC0, a.C[0]);
@@ -163,10 +162,10 @@ __device__ __forceinline__ void gw_walk(const float* __restrict__ go, int64_t pl
       tC2 = __fadd2_rn(tC2, a.C[2]);
     }
   }
-  v[0] = tSX.x + tSX.y;
+  v[0] = tSd.x + tSd.y;
   v[1] = tSY.x + tSY.y;
-  v[2] = tSXX.x + tSXX.y;
-  v[3] = tSXY.x + tSXY.y;
+  v[2] = tSdd.x + tSdd.y;
+  v[3] = tSdY.x + tSdY.y;
   v[4] = tSYY.x + tSYY.y;
   v[5] = tC0.x + tC0.y;
   v[6] = tC1.x + tC1.y;

@@ -1,0 +1,219 @@
+// Tile adjoint of the scale-aware 2D Gaussian render (GSASR, arXiv 2501.06838,
+// Eq. 4 with the Algorithm-1 window; differentiable render, Sec. 3.1 "Fast
+// Rasterization" and Sec. 3.2 "Rendering"), one lane per Gaussian.
+//
+// The exponent of a record is the completed square (log2 units, HR pixels)
+//   e = -d^2 + g Y^2 + l,   d = sA X - sK Y,   X = x - cx, Y = y - cy,
+// and the render adds c_k 2^e to channel k (c the record colour alpha * rgb).
+// For every (tile, Gaussian) pair of the forward's per-tile lists this kernel
+// adds the Gaussian's record-space moments over the tile's pixels,
+//   Sd = sum Gw d, SY = sum Gw Y, Sdd = sum Gw d^2, SdY = sum Gw d Y,
+//   SYY = sum Gw Y^2, C_k = sum g_k 2^e,   Gw = (sum_k g_k c_k) 2^e,
+// (g = dL/dI) to the Gaussian's accumulator with one atomic per value. The
+// moments are taken in the exponent's own coordinates (d, Y), not in (X, Y):
+// for |rho| -> 1 the X moments enter the chain rule with coefficients of
+// order 1/(1 - rho^2)^2 that cancel to order 1/(1 - rho^2), which float32
+// moments cannot resolve; in (d, Y) no such cancellation occurs.
+//
+// Layout: one warp per tile, walking the tile's list in chunks of 32 entries;
+// lane l owns the chunk's l-th Gaussian. The warp first stages the tile's
+// upstream gradient in shared memory, two columns per entry:
+//   sgA[r][j] = (g_r(2j), g_r(2j + 1), g_g(2j), g_g(2j + 1)),  sgB[r][j] = (g_b(2j), g_b(2j + 1)).
+// All lanes then walk the tile's pixels in the same order (row by row, two
+// columns at a time), so every shared-memory read is a broadcast, and each
+// lane evaluates its own Gaussian there in packed FP32x2 arithmetic:
+//   d = Xs - sK Y (one fused step), e = R - d^2, w = 2^e   (Xs = sA X per
+//   column, R = g Y^2 + l per row),
+//   G = g . c, C_k += g_k w, Gw = G w, per row A0 += Gw, A1 += Gw d, A2 += Gw d^2,
+// and after each row folds (A0, A1, A2) into the moments with that row's Y:
+//   SY += Y A0, SYY += Y^2 A0, Sd += A1, SdY += Y A1, Sdd += A2.
+// Per pixel that is 13 FP32 lane-operations (two pixels per packed
+// instruction) and one MUFU.EX2; no cross-lane reduction. Window masks are in
+// the operands (Xs = 1e18 outside the window's columns, so that d stays finite
+// and every product with w = +0 is 0; R = -inf outside its rows); rows that no
+// lane's window reaches are skipped.
+#include "gs_internal.cuh"
+
+namespace gs {
+
+namespace {
+
+constexpr float kInfG = __builtin_huge_valf();
+constexpr float kFarG = 1e18f;   // masked column: d^2 = 1e36 (finite), e = -1e36, w = +0
+
+__device__ __forceinline__ float2 p2(float a, float b) { return make_float2(a, b); }
+
+template <int TILE>
+__global__ void __launch_bounds__(32) k_raster_bwd_tile(Ws w, const uint32_t* vals) {
+  griddep_release();
+  griddep_wait();
+  constexpr int CP = TILE / 2;                 // column pairs per tile row
+  constexpr int SEG = TILE < 16 ? TILE : 16;   // columns per register table
+  constexpr int SP = SEG / 2;                  // column pairs per table
+  __shared__ float4 sgA[TILE * CP];
+  __shared__ float2 sgB[TILE * CP];
+
+  const int t = blockIdx.x;
+  const uint2 range = w.ranges[t];
+  const int n = (int)range.y - (int)range.x;
+  if (n <= 0) return;   // no Gaussian meets this tile (uniform)
+  const int lane = threadIdx.x;
+
+  // tile origin (image rows: a band's output holds rows row0 ..)
+  const int im = image_of_tile(w.images, w.n_images, t);
+  const ImageDesc* D = &w.images[im];
+  const int lt = t - D->t_base;
+  const int tyi = lt / D->tiles_x;
+  const int ox = (lt - tyi * D->tiles_x) * TILE;
+  const int oy = tyi * TILE + D->row0;
+
+  // the tile's upstream gradient (0 outside the output)
+  {
+    const int H = D->out_h, W = D->out_w;
+    const int64_t plane = (int64_t)H * W;
+    const float* go = w.direct ? w.grad_out0 : D->grad_out;
+    float* fa = reinterpret_cast<float*>(sgA);
+    float* fb = reinterpret_cast<float*>(sgB);
+    for (int idx = lane; idx < TILE * TILE; idx += 32) {
+      const int r = idx / TILE, x = idx - r * TILE;
+      const int gx = ox + x, gy = oy - D->row0 + r;
+      const bool in = gx < W && gy < H;
+      const int64_t o = in ? (int64_t)gy * W + gx : 0;   // always a valid address
+      const float vr = __ldg(go + o), vg = __ldg(go + plane + o), vb = __ldg(go + 2 * plane + o);
+      const int e = r * CP + (x >> 1), hb = x & 1;
+      fa[4 * e + hb] = in ? vr : 0.0f;
+      fa[4 * e + 2 + hb] = in ? vg : 0.0f;
+      fb[2 * e + hb] = in ? vb : 0.0f;
+    }
+  }
+  __syncwarp();
+
+  // A chunk's records are copied into shared memory (cp.async) while the
+  // chunk before it is computed, and its ids are loaded one chunk earlier
+  // still, so that no global-memory latency sits in front of a chunk.
+  __shared__ __align__(16) float4 srec[32][kRecordF4];
+  auto load_id = [&](int i) { return i < n ? __ldg(vals + range.x + i) : 0xffffffffu; };
+  auto copy_record = [&](uint32_t gid) {
+    if (gid < (uint32_t)w.n) {   // the list holds Gaussian ids
+      const float4* rec = w.records + (int64_t)gid * kRecordF4;
+#pragma unroll
+      for (int q = 0; q < kRecordF4; ++q) {
+        const unsigned dst = static_cast<unsigned>(__cvta_generic_to_shared(&srec[lane][q]));
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(rec + q) : "memory");
+      }
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  uint32_t gid_cur = load_id(lane);
+  uint32_t gid_next = load_id(32 + lane);
+  copy_record(gid_cur);
+  for (int base = 0; base < n; base += 32) {
+    const uint32_t gid = gid_cur;
+    const bool valid = gid < (uint32_t)w.n;
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncwarp();
+    float4 f[kRecordF4];
+#pragma unroll
+    for (int q = 0; q < kRecordF4; ++q) f[q] = srec[lane][q];
+    __syncwarp();
+    if (base + 32 < n) {
+      copy_record(gid_next);
+      gid_cur = gid_next;
+      gid_next = load_id(base + 64 + lane);
+    }
+    // the Gaussian's record in tile-local coordinates
+    float cxl = 0.f, cyl = 0.f, sA = 0.f, sK = 0.f, gy2 = 0.f, l = 0.f, cr = 0.f, cg = 0.f, cb = 0.f;
+    int lx0 = 1, lx1 = 0, ly0 = TILE, ly1 = -1;
+    if (valid) {
+      cxl = __fadd_rn(__fsub_rn(f[0].x, (float)ox), f[0].y);
+      cyl = __fadd_rn(__fsub_rn(f[0].z, (float)oy), f[0].w);
+      sA = f[1].x; sK = f[1].y; gy2 = f[1].z; l = f[1].w;
+      cr = f[2].x; cg = f[2].y; cb = f[2].z;
+      lx0 = max(__float_as_int(f[3].x) - ox, 0);
+      lx1 = min(__float_as_int(f[3].y) - ox, TILE - 1);
+      ly0 = max(__float_as_int(f[3].z) - oy, 0);
+      ly1 = min(__float_as_int(f[3].w) - oy, TILE - 1);
+      if (lx0 > lx1 || ly0 > ly1) { ly0 = TILE; ly1 = -1; }
+    }
+    // rows some lane's window reaches
+    const int rlo = __reduce_min_sync(0xffffffffu, ly0);
+    const int rhi = __reduce_max_sync(0xffffffffu, ly1);
+    const float2 cr2 = p2(cr, cr), cg2 = p2(cg, cg), cb2 = p2(cb, cb), nsK2 = p2(-sK, -sK);
+    float2 Cr = p2(0.f, 0.f), Cg = Cr, Cb = Cr;
+    // moments, the two columns of a pair kept apart until the end
+    float2 Sd = p2(0.f, 0.f), SY = Sd, Sdd = Sd, SdY = Sd, SYY = Sd;
+#pragma unroll
+    for (int seg = 0; seg < TILE / SEG; ++seg) {
+      // per column pair: Xs = sA X (kFarG outside the window)
+      float2 Xs2[SP];
+#pragma unroll
+      for (int j = 0; j < SP; ++j) {
+        const int c0 = seg * SEG + 2 * j, c1 = c0 + 1;
+        const float a = __fsub_rn((float)c0, cxl), b = __fsub_rn((float)c1, cxl);
+        Xs2[j] = p2((c0 >= lx0 && c0 <= lx1) ? sA * a : kFarG,
+                    (c1 >= lx0 && c1 <= lx1) ? sA * b : kFarG);
+      }
+      for (int r = rlo; r <= rhi; ++r) {
+        const float Y = __fsub_rn((float)r, cyl);
+        const float R = (r >= ly0 && r <= ly1) ? fmaf(gy2 * Y, Y, l) : -kInfG;
+        const float2 Y2 = p2(Y, Y), R2 = p2(R, R);
+        const float4* ga = sgA + r * CP + seg * SP;
+        const float2* gb = sgB + r * CP + seg * SP;
+        float2 A0, A1, A2;
+#pragma unroll
+        for (int j = 0; j < SP; ++j) {
+          const float4 q = ga[j];
+          const float2 gbj = gb[j];
+          const float2 gr2 = p2(q.x, q.y), gg2 = p2(q.z, q.w);
+          const float2 d = __ffma2_rn(nsK2, Y2, Xs2[j]);   // one rounding: d cancels for |rho| -> 1
+          const float2 e = __ffma2_rn(p2(-d.x, -d.y), d, R2);
+          const float2 wv = p2(ex2_approx(e.x), ex2_approx(e.y));
+          const float2 G = __ffma2_rn(gbj, cb2, __ffma2_rn(gg2, cg2, __fmul2_rn(gr2, cr2)));
+          Cr = __ffma2_rn(gr2, wv, Cr);
+          Cg = __ffma2_rn(gg2, wv, Cg);
+          Cb = __ffma2_rn(gbj, wv, Cb);
+          const float2 Gw = __fmul2_rn(G, wv);
+          const float2 Gwd = __fmul2_rn(Gw, d);
+          if (j == 0) {
+            A0 = Gw;
+            A1 = Gwd;
+            A2 = __fmul2_rn(Gwd, d);
+          } else {
+            A0 = __fadd2_rn(A0, Gw);
+            A1 = __fadd2_rn(A1, Gwd);
+            A2 = __ffma2_rn(Gwd, d, A2);
+          }
+        }
+        const float2 ty = __fmul2_rn(Y2, A0);
+        SY = __fadd2_rn(SY, ty);
+        SYY = __ffma2_rn(ty, Y2, SYY);
+        Sd = __fadd2_rn(Sd, A1);
+        SdY = __ffma2_rn(Y2, A1, SdY);
+        Sdd = __fadd2_rn(Sdd, A2);
+      }
+    }
+    if (valid) {
+      const float v[8] = {Sd.x + Sd.y, SY.x + SY.y, Sdd.x + Sdd.y, SdY.x + SdY.y, SYY.x + SYY.y,
+                          Cr.x + Cr.y, Cg.x + Cg.y, Cb.x + Cb.y};
+      float* acc = w.grec + (int64_t)gid * 12;
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (v[k] != 0.0f) atomicAdd(acc + k, v[k]);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_raster_bwd_tile(const Ws& w, const uint32_t* lists, cudaStream_t s) {
+  if (w.tiles == 0) return cudaSuccess;
+  LaunchScope ls(kKRasterBwd, s);
+  const dim3 grid((unsigned)w.tiles), block(32);
+  switch (w.tile) {
+    case 8: return launch_chain(k_raster_bwd_tile<8>, grid, block, 0, s, w, lists);
+    case 32: return launch_chain(k_raster_bwd_tile<32>, grid, block, 0, s, w, lists);
+    default: return launch_chain(k_raster_bwd_tile<16>, grid, block, 0, s, w, lists);
+  }
+}
+
+}  // namespace gs

@@ -115,7 +115,7 @@ Layout make_layout(int n_images, int64_t n, int64_t tiles, int64_t capacity, boo
 }
 
 int tile_of(const gs_view& v) { return v.tile == 0 ? 16 : v.tile; }
-int batch_of(const gs_view& v) { return v.batch == 0 ? 32 : v.batch; }
+int batch_of(const gs_view& v) { return v.batch; }   // 0: the tile's smaller batch
 int shift_of(int tile) { return tile == 8 ? 3 : tile == 32 ? 5 : 4; }
 
 struct Problem {
@@ -190,8 +190,15 @@ gs_status validate(int32_t n_images, const gs_gaussians* g, const gs_view* v, Pr
   }
   if (!(P->tile == 8 || P->tile == 16 || P->tile == 32))
     return fail(GS_ERR_INVALID, "tile must be 8, 16 or 32 (got %lld)", (long long)P->tile);
-  if (P->batch < 32 || P->batch > 512)
-    return fail(GS_ERR_INVALID, "batch must be in [32, 512] (got %lld)", (long long)P->batch);
+  // the raster stages one or two Gaussians per thread of its block per round
+  // (32 threads at tile 8 and 16, 64 at tile 32): only those batches run
+  const bool batch_ok = P->batch == 0 || (P->tile == 32 ? (P->batch == 64 || P->batch == 128)
+                                                         : (P->batch == 32 || P->batch == 64));
+  if (!batch_ok)
+    return fail(GS_ERR_INVALID,
+                "batch must be 0 (default) or a batch the raster runs: 32 or 64 Gaussians per "
+                "shared-memory round at tile 8 and 16, 64 or 128 at tile 32 (got %lld at tile %lld)",
+                (long long)P->batch, (long long)P->tile);
   if (v[0].binning == GS_BINNING_GRID && !grid_ok)
     return fail(GS_ERR_UNSUPPORTED,
                 "grid binning needs every image on a reference grid (ref_grid_m > 0) and outputs "
@@ -399,7 +406,7 @@ gs_status run_backward(int32_t n_images, const gs_gaussians* g, const gs_view* v
     e = launch_zero(c.w.grec, 48 * (size_t)c.w.n, s);
     if (e != cudaSuccess) return cuda_fail(e, "memset");
     const int fb = c.passes & 1;
-    e = launch_raster_bwd(c.w, c.w.grid ? c.w.vals[0] : c.w.vals[fb], c.P.batch, s);
+    e = launch_raster_bwd_tile(c.w, c.w.grid ? c.w.vals[0] : c.w.vals[fb], s);
     if (e != cudaSuccess) return cuda_fail(e, "raster_bwd");
   } else {
     // one warp per Gaussian writes all its moments: no clearing, no atomics

@@ -222,8 +222,8 @@ cudaError_t launch_emit(const Ws& w, cudaStream_t s);
 cudaError_t launch_sort(const Ws& w, int key_bits, cudaStream_t s, int* final_buf);
 cudaError_t launch_ranges(const Ws& w, const uint32_t* sorted_keys, cudaStream_t s);
 cudaError_t launch_raster_fwd(const Ws& w, const uint32_t* sorted_vals, int batch, cudaStream_t s);
-cudaError_t launch_raster_bwd(const Ws& w, const uint32_t* sorted_vals, int batch, cudaStream_t s);
 cudaError_t launch_raster_bwd_gw(const Ws& w, cudaStream_t s);
+cudaError_t launch_raster_bwd_tile(const Ws& w, const uint32_t* lists, cudaStream_t s);
 
 // Kernel ids for launch accounting / per-kernel timing.
 enum KernelId {

@@ -9,10 +9,10 @@
 // The array is a file-scope __device__ variable of kNoallocScratchBytes. Every
 // GPU that loads this module holds it until the process exits. Host code never
 // dereferences or passes the symbol itself (on the host it is only a stand-in,
-// not a device address): the device address is looked up once per device with
-// cudaGetSymbolAddress and cached.
+// not a device address): every call looks up the array's device address on the
+// current device with cudaGetSymbolAddress, so that a context created again
+// (after cudaDeviceReset, say) never leaves a stale address behind.
 #include <cstdio>
-#include <mutex>
 
 #include "../../include/gs.h"
 #include "gs_internal.cuh"
@@ -24,38 +24,25 @@ void set_last_error(const char* msg);
 namespace {
 
 constexpr size_t kNoallocScratchBytes = size_t(64) << 20;   // 64 MiB
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
-
-std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[kMaxDevices] = {};
 
 gs_status noalloc_fail(gs_status st, const char* msg) {
   gs::set_last_error(msg);
   return st;
 }
 
-// Device address of the scratch array on the current device; looked up on the
-// first call made with that device current, then cached.
+// Device address of the scratch array in the current device's context.
 gs_status noalloc_scratch(void** out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return noalloc_fail(GS_ERR_CUDA, cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(GS_ERR_UNSUPPORTED, "device index >= 64");
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      char buf[256];
-      std::snprintf(buf, sizeof(buf), "cudaGetSymbolAddress of the static scratch failed: %s",
-                    cudaGetErrorString(e));
-      return noalloc_fail(GS_ERR_CUDA, buf);
-    }
-    g_noalloc_ptr[dev] = p;
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "cudaGetSymbolAddress of the static scratch failed: %s",
+                  cudaGetErrorString(e));
+    return noalloc_fail(GS_ERR_CUDA, buf);
   }
-  *out = g_noalloc_ptr[dev];
+  *out = p;
   return GS_OK;
 }
 
@@ -84,6 +71,9 @@ extern "C" gs_status gs_render_fwd_noalloc(const gs_gaussians* g, const gs_view*
   if (st != GS_OK) return st;
   const size_t need = gs_workspace_size(1, g, v, pairs);
   if (need == 0 || need > kNoallocScratchBytes) {
+    // the count itself flagged the overflow in the array's status word; the
+    // refusal reports it, so clear it for the next status read
+    gs_sync_status(ws, stream);
     std::snprintf(buf, sizeof(buf),
                   "gs_render_fwd_noalloc: %lld (tile, Gaussian) pairs need %zu bytes of scratch; "
                   "the static scratch holds %zu bytes",
@@ -93,4 +83,15 @@ extern "C" gs_status gs_render_fwd_noalloc(const gs_gaussians* g, const gs_view*
   // The render resets the scratch header itself and clears its tile ranges;
   // every other scratch byte is written before it is read.
   return gs_render_fwd(g, v, out, ws, kNoallocScratchBytes, stream);
+}
+
+// The status word the kernels of the last gs_render_fwd_noalloc left in the
+// static scratch (a count above the capacity, an internal check): the caller
+// has no workspace pointer to give gs_sync_status, so this reads the scratch's
+// header through the same symbol lookup, then resets it.
+extern "C" gs_status gs_noalloc_sync_status(void* stream) {
+  void* ws = nullptr;
+  const gs_status st = noalloc_scratch(&ws);
+  if (st != GS_OK) return st;
+  return gs_sync_status(ws, stream);
 }

@@ -391,17 +391,25 @@ __global__ void __launch_bounds__(kFootprintBlock) k_preprocess(Ws w) {
 }
 
 // Chain rule from the record space to the parameters. The raster adjoint left,
-// per Gaussian, the moments of Gw = (sum_k g_k c_k) 2^e over its window
-//   m = (SX, SY, SXX, SXY, SYY, Cr, Cg, Cb),
-//   S_ab = sum Gw X^a Y^b, C_k = sum g_k 2^e, and S0 = sum Gw = c . C
-// (c the record colour alpha * rgb).
-// With out_k += c_k 2^e and e = A X^2 + B X Y + C Y^2 + l (the record's
-// completed-square form expands to this):
-//   dL/dl = ln2 S0, dL/dA = ln2 SXX, dL/dB = ln2 SXY, dL/dC = ln2 SYY,
-//   dL/dcx = -ln2 (2A SX + B SY), dL/dcy = -ln2 (B SX + 2C SY),
-// and cx = s mu_x, A = -L2/(2 s^2 sx^2 D), B = L2 rho/(s^2 sx sy D),
-// C = -L2/(2 s^2 sy^2 D), l = -log2(2 pi sx sy sqrt D) (density) or 0 (peak),
-// colour record = alpha c (L2 = log2 e, so ln2 * L2 = 1).
+// per Gaussian, the moments over its window of Gw = (sum_k g_k c_k) 2^e in the
+// exponent's completed-square coordinates,
+//   m = (Sd, SY, Sdd, SdY, SYY, Cr, Cg, Cb),  S_ab = sum Gw d^a Y^b,
+//   C_k = sum g_k 2^e, and S0 = sum Gw = c . C,
+// with e = -d^2 + g Y^2 + l, d = sA X - sK Y, X = x - cx, Y = y - cy, and
+// out_k += c_k 2^e (c the record colour alpha * rgb). Since dL/de = ln2 Gw:
+//   dL/dcx = 2 ln2 sA Sd,            dL/dcy = -2 ln2 (sK Sd + g SY),
+//   dL/dsA = -2 ln2 (Sdd + sK SdY) / sA   (X = (d + sK Y) / sA),
+//   dL/dsK = 2 ln2 SdY,  dL/dg = ln2 SYY,  dL/dl = ln2 S0.
+// With sA = r / (s sx), sK = rho r / (s sy), g = -L2 / (2 s^2 sy^2),
+// r = sqrt(L2 / (2 D)), D = (1 - rho)(1 + rho), L2 = log2 e, and
+// l = -log2(2 pi sx sy sqrt D) (density; 0 for the peak reading):
+//   dL/dsx  = (2 ln2 (Sdd + sK SdY) - S0) / sx
+//   dL/dsy  = (-2 ln2 (sK SdY + g SYY) - S0) / sy
+//   dL/drho = rho (S0 - 2 ln2 Sdd) / D + 2 ln2 SdY r / (s sy)
+// (the S0 terms only with the density normalisation; dsA/drho = sA rho / D,
+// dsK/drho = r / (s sy D), dl/drho = rho / (D ln2)), and cx = s mu_x.
+// No term cancels at order 1/D^2 as |rho| -> 1, which the same chain rule in
+// the moments of X would.
 __global__ void __launch_bounds__(256) k_preprocess_bwd(Ws w) {
   griddep_release();
   griddep_wait();
@@ -426,26 +434,25 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(Ws w) {
   const float s = D.scale;
   const float Dr = P.D;
   const float isx = __frcp_rn(__fmul_rn(s, sx)), isy = __frcp_rn(__fmul_rn(s, sy));
-  const float q = __fdiv_rn(kLog2E, Dr);
-  const float A = -0.5f * q * isx * isx;
-  const float B = q * rho * isx * isy;
-  const float C = -0.5f * q * isy * isy;
+  // the record's exponent constants, as the footprint pass forms them
+  const float r = sqrtf(__fdiv_rn(0.5f * kLog2E, Dr));
+  const float sA = r * isx;
+  const float sK = rho * r * isy;
+  const float gY = -0.5f * kLog2E * isy * isy;
   const float4* gm = reinterpret_cast<const float4*>(w.grec + gi * 12);
   const float4 m0 = gm[0], m1 = gm[1];
-  const float SX = m0.x, SY = m0.y, SXX = m0.z, SXY = m0.w, SYY = m1.x;
+  const float Sd = m0.x, SY = m0.y, Sdd = m0.z, SdY = m0.w, SYY = m1.x;
   const float Cr = m1.y, Cg = m1.z, Cb = m1.w;
   const float4 rc = rec[2];
   const float S0 = fmaf(rc.z, Cb, fmaf(rc.y, Cg, rc.x * Cr));
 
-  const float dcx = -kLn2 * (2.0f * A * SX + B * SY);
-  const float dcy = -kLn2 * (B * SX + 2.0f * C * SY);
+  const float two_ln2 = 2.0f * kLn2;
+  const float dcx = two_ln2 * sA * Sd;
+  const float dcy = -two_ln2 * fmaf(sK, Sd, gY * SY);
   const float dens = (D.flags & kFlagPeak) == 0 ? 1.0f : 0.0f;
-  const float dsx = (kLn2 * (-2.0f * A * SXX - B * SXY) - dens * S0) / sx;
-  const float dsy = (kLn2 * (-2.0f * C * SYY - B * SXY) - dens * S0) / sy;
-  const float two_r_over_D = 2.0f * rho / Dr;
-  const float drho = kLn2 * two_r_over_D * (A * SXX + C * SYY) +
-                     SXY * (1.0f + rho * rho) / (s * s * sx * sy * Dr * Dr) +
-                     dens * S0 * rho / Dr;
+  const float dsx = (two_ln2 * fmaf(sK, SdY, Sdd) - dens * S0) / sx;
+  const float dsy = (-two_ln2 * fmaf(sK, SdY, gY * SYY) - dens * S0) / sy;
+  const float drho = rho * fmaf(-two_ln2, Sdd, dens * S0) / Dr + two_ln2 * SdY * r * isy;
   float gr[9] = {s * dcx, s * dcy, dsx, dsy, drho, al * Cr, al * Cg, al * Cb,
                  cr * Cr + cg * Cg + cb * Cb};
   if (D.flags & kFlagHead) {   // chain rule through the head's activations

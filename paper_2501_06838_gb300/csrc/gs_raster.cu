@@ -1,5 +1,6 @@
 // Tile rasterizer of the scale-aware 2D Gaussian splatting render (GSASR,
-// arXiv 2501.06838, Eq. 4 with the Algorithm-1 window) and its adjoint.
+// arXiv 2501.06838, Eq. 4 with the Algorithm-1 window): the forward. (The
+// adjoint, one lane per Gaussian over a tile's pixels, is gs_adjoint_tile.cu.)
 //
 // One CTA of NT = TILE*TILE/BY threads renders one TILE x TILE tile of HR
 // pixels; thread t owns column t % TILE and the BY consecutive rows
@@ -13,10 +14,8 @@
 //            float32 precision even at x ~ 5760) and clips its window;
 //   stage 2: per (Gaussian, pair of tile rows) the row terms of the exponent
 //              e = -(sA X - sK Y)^2 + g Y^2 + l        (log2 units)
-//            as one float4: (-K(r), -K(r+1), R(r), R(r+1)) for the forward
-//            and (Y(r), Y(r+1), R(r), R(r+1)) for the adjoint, which needs Y
-//            itself, with K = sK*Y and R = g*Y^2 + l (R = -inf outside the
-//            window rows);
+//            as one float4 (-K(r), -K(r+1), R(r), R(r+1)), with K = sK*Y and
+//            R = g*Y^2 + l (R = -inf outside the window rows);
 //   compute: per Gaussian each thread forms Xs = sA*(col - cxl) (+inf outside
 //            the window columns) and, for each of its row pairs, in packed
 //            FP32x2 arithmetic (one instruction for both rows),
@@ -190,13 +189,10 @@ __device__ __forceinline__ void grid_source_init(const Ws& w, const ImageDesc* D
 }
 
 // Stage 1 from the raw records:
-//   gA = (cxl, sA, lx0, lx1)   gB = (cyl, sK, g, l)
-//   forward: gC = (r, g, b, ly0 | ly1 << 16)
-//   adjoint: gC = (r, r, g, g), gD = (b, b, -sK, ly0 | ly1 << 16) (colours
-//            duplicated so that they are ready-made FP32x2 operands).
-template <int TILE, int NT, bool DUP>
+//   gA = (cxl, sA, lx0, lx1)   gB = (cyl, sK, g, l)   gC = (r, g, b, ly0 | ly1 << 16)
+template <int TILE, int NT>
 __device__ __forceinline__ void stage_records(const float4* raw, int nb, int ox, int oy,
-                                              float4* gA, float4* gB, float4* gC, float4* gD) {
+                                              float4* gA, float4* gB, float4* gC) {
   for (int i = threadIdx.x; i < nb; i += NT) {
     const float4 f0 = raw[i * kRecordF4], f1 = raw[i * kRecordF4 + 1];
     const float4 f2 = raw[i * kRecordF4 + 2], f3 = raw[i * kRecordF4 + 3];
@@ -206,34 +202,27 @@ __device__ __forceinline__ void stage_records(const float4* raw, int nb, int ox,
     const int ly0 = max(__float_as_int(f3.z) - oy, 0), ly1 = min(__float_as_int(f3.w) - oy, TILE - 1);
     gA[i] = make_float4(cxl, f1.x, (float)lx0, (float)lx1);
     gB[i] = make_float4(cyl, f1.y, f1.z, f1.w);
-    const float pk = __int_as_float(ly0 | (ly1 << 16));
-    if (DUP) {
-      gC[i] = make_float4(f2.x, f2.x, f2.y, f2.y);
-      gD[i] = make_float4(f2.z, f2.z, -f1.y, pk);
-    } else {
-      gC[i] = make_float4(f2.x, f2.y, f2.z, pk);
-    }
+    gC[i] = make_float4(f2.x, f2.y, f2.z, __int_as_float(ly0 | (ly1 << 16)));
   }
 }
 
-// Stage 2: row terms of every staged Gaussian and pair of tile rows, as
-// (-K(2p), -K(2p+1), R(2p), R(2p+1)) or, with YT, (Y(2p), Y(2p+1), R(2p),
-// R(2p+1)); the packed window rows come from gP[i].w.
-template <int TILE, int NT, bool YT>
-__device__ __forceinline__ void stage_rowpairs(int nb, const float4* gB, const float4* gP,
+// Stage 2: row terms (-K(2p), -K(2p+1), R(2p), R(2p+1)) of every staged
+// Gaussian and pair of tile rows; the packed window rows come from gC[i].w.
+template <int TILE, int NT>
+__device__ __forceinline__ void stage_rowpairs(int nb, const float4* gB, const float4* gC,
                                                float4* rq) {
   constexpr int HP = TILE / 2;
   for (int idx = threadIdx.x; idx < nb * HP; idx += NT) {
     const int i = idx / HP, p = idx - i * HP;
     const float4 b = gB[i];
-    const int pk = __float_as_int(gP[i].w);
+    const int pk = __float_as_int(gC[i].w);
     const int ly0 = pk & 0xffff, ly1 = pk >> 16;
     const int r0 = 2 * p, r1 = 2 * p + 1;
     const float Y0 = (float)r0 - b.x, Y1 = (float)r1 - b.x;
     float R0 = fmaf(b.z * Y0, Y0, b.w), R1 = fmaf(b.z * Y1, Y1, b.w);
     if (r0 < ly0 || r0 > ly1) R0 = -kInf;
     if (r1 < ly0 || r1 > ly1) R1 = -kInf;
-    rq[idx] = YT ? make_float4(Y0, Y1, R0, R1) : make_float4(-b.y * Y0, -b.y * Y1, R0, R1);
+    rq[idx] = make_float4(-b.y * Y0, -b.y * Y1, R0, R1);
   }
 }
 
@@ -361,9 +350,9 @@ __global__ void __launch_bounds__(TILE * TILE / BY) k_raster_fwd(Ws w, const uin
     const int nb = min(BATCH, total - b * BATCH);
     cp_async_wait_all();
     __syncthreads();
-    stage_records<TILE, NT, false>(raw[b & 1], nb, ox, oy, gA, gB, gC, nullptr);
+    stage_records<TILE, NT>(raw[b & 1], nb, ox, oy, gA, gB, gC);
     __syncthreads();
-    stage_rowpairs<TILE, NT, false>(nb, gB, gC, rq);
+    stage_rowpairs<TILE, NT>(nb, gB, gC, rq);
     __syncthreads();
     if (b + 1 < nbat) {
       issue_records<NT, PF>(w, gid, min(BATCH, total - (b + 1) * BATCH), raw[(b + 1) & 1]);
@@ -401,231 +390,33 @@ __global__ void __launch_bounds__(TILE * TILE / BY) k_raster_fwd(Ws w, const uin
   }
 }
 
-// Adjoint. Each thread holds dL/dI of its pixels; per staged Gaussian it
-// accumulates, over its pixels, with Gw = (g . c) 2^e,
-//   SY = sum Gw Y, SYY = sum Gw Y^2, C_k = sum g_k 2^e,
-// and forms S0 = sum Gw = c . C, then (its X is fixed) SX = X S0, SXX = X SX,
-// SXY = X SY. Y = y - cy comes with the row terms (d = sA X - sK Y is then
-// one FFMA2 per row pair).
-// Eight values per Gaussian leave the tile (SX, SY, SXX, SXY, SYY, C_r, C_g,
-// C_b); S0 is linear in C (S0 = c . C) and is rebuilt from the summed C.
-// Reduction over each warp's 32 lanes, batched over kRB = 4 Gaussians (32
-// rows): lanes store their eight values transposed in shared memory (row
-// (g, f) holds the 32 lane values, padded to 36 floats so that rows start on
-// 16-byte boundaries), then lane j sums row j with eight 16-byte loads and
-// adds the total to the Gaussian's record-space accumulator: one atomic per
-// (tile, Gaussian, value) and warp.
-constexpr int kNV = 8;            // values per Gaussian leaving a tile
-constexpr int kRB = 4;            // Gaussians per reduction round (kRB * kNV = 32 rows)
-constexpr int kRedRow = 36;       // row of 32 lane values, padded to a 16-byte multiple
-
-template <int NQ>
-struct BwdOps {
-  float4 a, c, e, q[NQ];
-  __device__ __forceinline__ void load(const float4* gA, const float4* gC, const float4* gD,
-                                       const float4* rq, int i, int hp, int pair0) {
-    a = gA[i];
-    c = gC[i];
-    e = gD[i];
-    const float4* rr = rq + i * hp + pair0;
-#pragma unroll
-    for (int j = 0; j < NQ; ++j) q[j] = rr[j];
-  }
-};
-
-// The eight record-space moments of one Gaussian over this thread's pixels,
-// two rows at a time in packed FP32x2 arithmetic. g[j][ch] holds dL/dI of
-// channel ch at rows (2j, 2j + 1).
-template <int NQ>
-__device__ __forceinline__ void bwd_gaussian(const float2 (&g)[NQ][3], const BwdOps<NQ>& o,
-                                             float fcol, float (&v)[kNV]) {
-  const float Xr = fcol - o.a.x;
-  const float Xs = (fcol < o.a.z || fcol > o.a.w) ? kInf : o.a.y * Xr;
-  const float2 X2 = f2(Xs, Xs);
-  const float2 nsK = f2(o.e.z, o.e.z);
-  const float2 cr = f2(o.c.x, o.c.y), cg = f2(o.c.z, o.c.w), cb = f2(o.e.x, o.e.y);
-  float2 SY = f2(0.f, 0.f), SYY = SY, Cr = SY, Cg = SY, Cb = SY;
-#pragma unroll
-  for (int j = 0; j < NQ; ++j) {
-    const float2 Y = f2(o.q[j].x, o.q[j].y);
-    const float2 d = __ffma2_rn(nsK, Y, X2);
-    const float2 e = __ffma2_rn(f2(-d.x, -d.y), d, f2(o.q[j].z, o.q[j].w));
-    const float2 wv = f2(ex2_approx(e.x), ex2_approx(e.y));
-    const float2 G = __ffma2_rn(g[j][2], cb, __ffma2_rn(g[j][1], cg, __fmul2_rn(g[j][0], cr)));
-    const float2 GwY = __fmul2_rn(__fmul2_rn(G, wv), Y);
-    SY = __fadd2_rn(SY, GwY);
-    SYY = __ffma2_rn(GwY, Y, SYY);
-    Cr = __ffma2_rn(g[j][0], wv, Cr);
-    Cg = __ffma2_rn(g[j][1], wv, Cg);
-    Cb = __ffma2_rn(g[j][2], wv, Cb);
-  }
-  const float cR = Cr.x + Cr.y, cG = Cg.x + Cg.y, cB = Cb.x + Cb.y;
-  const float S0 = fmaf(o.e.x, cB, fmaf(o.c.z, cG, o.c.x * cR));
-  const float sy = SY.x + SY.y;
-  v[0] = Xr * S0;
-  v[1] = sy;
-  v[2] = Xr * v[0];
-  v[3] = Xr * sy;
-  v[4] = SYY.x + SYY.y;
-  v[5] = cR;
-  v[6] = cG;
-  v[7] = cB;
-}
-
 template <int TILE, int BY, int PF>
-__global__ void __launch_bounds__(TILE * TILE / BY) k_raster_bwd(Ws w, const uint32_t* vals) {
-  griddep_release();
-  griddep_wait();
-  constexpr int NT = TILE * TILE / BY, NW = NT / 32, BATCH = NT * PF, NQ = BY / 2, HP = TILE / 2;
-  __shared__ __align__(16) float4 raw[2][BATCH * kRecordF4];
-  __shared__ float4 gA[BATCH], gB[BATCH], gC[BATCH], gD[BATCH];
-  __shared__ float4 rq[BATCH * HP];
-  __shared__ __align__(16) float red[NW][kRB * kNV * kRedRow];
-  __shared__ uint32_t gids[2][BATCH];
-
-  const ImageDesc* D;
-  int ox, oy;
-  tile_origin<TILE>(w, blockIdx.x, D, ox, oy);
-  SortedSource<NT, PF> src;
-  {
-    const uint2 range = w.ranges[blockIdx.x];
-    if (range.y <= range.x) return;
-    src.vals = vals;
-    src.pos = (int)range.x;
-    src.end = (int)range.y;
-  }
-  const int col = threadIdx.x % TILE;
-  const int row0 = (threadIdx.x / TILE) * BY;
-  const int pair0 = row0 / 2;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const float fcol = (float)col;
-  float* wred = red[warp];
-  // rows covered by this warp, for skipping Gaussians that miss them (NW > 1)
-  const int wrow0 = ((threadIdx.x & ~31) / TILE) * BY;
-  const int wrow1 = min(TILE - 1, (((threadIdx.x | 31) / TILE) + 1) * BY - 1);
-
-  float2 g[NQ][3];
-  {
-    const int H = D->out_h, W = D->out_w;
-    const int x = ox + col;
-    const int64_t plane = (int64_t)H * W;
-#pragma unroll
-    for (int k = 0; k < BY; ++k) {
-      const int y = oy - D->row0 + row0 + k;   // output row
-      const bool in = x < W && y < H;
-      const int64_t o = (int64_t)y * W + x;
-      float* gk = reinterpret_cast<float*>(&g[k / 2][0]) + (k & 1);
-      const float* go = w.direct ? w.grad_out0 : D->grad_out;
-      gk[0] = in ? __ldg(go + o) : 0.0f;
-      gk[2] = in ? __ldg(go + plane + o) : 0.0f;
-      gk[4] = in ? __ldg(go + 2 * plane + o) : 0.0f;
-    }
-  }
-
-  uint32_t gid[PF];
-  int nb = src.next(gid);      // batch 0
-  int nb1 = 0;
-  if (nb > 0) {
-#pragma unroll
-    for (int j = 0; j < PF; ++j) gids[0][j * NT + threadIdx.x] = gid[j];
-    issue_records<NT, PF>(w, gid, nb, raw[0]);
-    nb1 = src.next(gid);        // batch 1
-  }
-  for (int b = 0; nb > 0; ++b) {
-    cp_async_wait_all();
-    __syncthreads();
-    stage_records<TILE, NT, true>(raw[b & 1], nb, ox, oy, gA, gB, gC, gD);
-    __syncthreads();
-    stage_rowpairs<TILE, NT, true>(nb, gB, gD, rq);
-    __syncthreads();
-    int nb2 = 0;
-    if (nb1 > 0) {
-#pragma unroll
-      for (int j = 0; j < PF; ++j) gids[(b + 1) & 1][j * NT + threadIdx.x] = gid[j];
-      issue_records<NT, PF>(w, gid, nb1, raw[(b + 1) & 1]);
-      nb2 = src.next(gid);      // batch b + 2
-    }
-    const uint32_t* bgid = gids[b & 1];
-    // One Gaussian: its moments, staged for the warp reduction; every kRB
-    // Gaussians (and at the end of the batch) the warp reduces and adds.
-    auto process = [&](const BwdOps<NQ>& o, int i) {
-      float v[kNV] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      const int pk = __float_as_int(o.e.w);
-      if (NW == 1 || ((pk >> 16) >= wrow0 && (pk & 0xffff) <= wrow1))   // warp-uniform
-        bwd_gaussian<NQ>(g, o, fcol, v);
-      const int slot = i % kRB;
-#pragma unroll
-      for (int f = 0; f < kNV; ++f) wred[(slot * kNV + f) * kRedRow + lane] = v[f];
-      if (slot == kRB - 1 || i == nb - 1) {   // block-uniform
-        __syncwarp();
-        if (lane < (slot + 1) * kNV) {
-          const float4* src = reinterpret_cast<const float4*>(wred + lane * kRedRow);
-          float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-#pragma unroll
-          for (int l = 0; l < 8; ++l) {
-            const float4 t = src[l];
-            s0 += t.x;
-            s1 += t.y;
-            s2 += t.z;
-            s3 += t.w;
-          }
-          const float s = (s0 + s1) + (s2 + s3);
-          const int gi = i - slot + lane / kNV;
-          if (s != 0.0f) atomicAdd(w.grec + (int64_t)bgid[gi] * 12 + (lane % kNV), s);
-        }
-        __syncwarp();
-      }
-    };
-    // Two operand sets in registers: Gaussian i + 1's loads overlap i's math.
-    BwdOps<NQ> A, B;
-    A.load(gA, gC, gD, rq, 0, HP, pair0);
-    for (int i = 0; i < nb; i += 2) {
-      if (i + 1 < nb) B.load(gA, gC, gD, rq, i + 1, HP, pair0);
-      process(A, i);
-      if (i + 1 >= nb) break;
-      if (i + 2 < nb) A.load(gA, gC, gD, rq, i + 2, HP, pair0);
-      process(B, i + 1);
-    }
-    __syncthreads();
-    nb = nb1;
-    nb1 = nb2;
-  }
-}
-
-template <int TILE, int BY, int PF>
-cudaError_t run(const Ws& w, const uint32_t* vals, bool bwd, cudaStream_t s) {
+cudaError_t run(const Ws& w, const uint32_t* vals, cudaStream_t s) {
   constexpr int NT = TILE * TILE / BY;
-  if (bwd) {
-    LaunchScope ls(kKRasterBwd, s);
-    return launch_chain(k_raster_bwd<TILE, BY, PF>, dim3(w.tiles), dim3(NT), 0, s, w, vals);
-  }
   LaunchScope ls(kKRasterFwd, s);
   if (w.grid) return launch_chain(k_raster_fwd<TILE, BY, PF, true>, dim3(w.tiles), dim3(NT), 0, s, w, vals);
   return launch_chain(k_raster_fwd<TILE, BY, PF, false>, dim3(w.tiles), dim3(NT), 0, s, w, vals);
 }
 
 // Launch configurations: tile edge -> rows per thread (threads = TILE^2 / BY);
-// batch = Gaussians staged per round = threads * PF, PF in {1, 2}.
-cudaError_t dispatch(const Ws& w, const uint32_t* vals, int batch, bool bwd, cudaStream_t s) {
+// batch = Gaussians staged per round = threads * PF, PF in {1, 2} (the host
+// accepts only these batches; 0 selects PF = 1).
+cudaError_t dispatch(const Ws& w, const uint32_t* vals, int batch, cudaStream_t s) {
   if (w.tiles == 0) return cudaSuccess;
   switch (w.tile) {
     case 8:   // 32 threads
-      return batch >= 64 ? run<8, 2, 2>(w, vals, bwd, s) : run<8, 2, 1>(w, vals, bwd, s);
+      return batch >= 64 ? run<8, 2, 2>(w, vals, s) : run<8, 2, 1>(w, vals, s);
     case 32:  // 64 threads
-      return batch >= 128 ? run<32, 16, 2>(w, vals, bwd, s) : run<32, 16, 1>(w, vals, bwd, s);
+      return batch >= 128 ? run<32, 16, 2>(w, vals, s) : run<32, 16, 1>(w, vals, s);
     default:  // 32 threads
-      return batch >= 64 ? run<16, 8, 2>(w, vals, bwd, s) : run<16, 8, 1>(w, vals, bwd, s);
+      return batch >= 64 ? run<16, 8, 2>(w, vals, s) : run<16, 8, 1>(w, vals, s);
   }
 }
 
 }  // namespace
 
 cudaError_t launch_raster_fwd(const Ws& w, const uint32_t* vals, int batch, cudaStream_t s) {
-  return dispatch(w, vals, batch, false, s);
-}
-
-cudaError_t launch_raster_bwd(const Ws& w, const uint32_t* vals, int batch, cudaStream_t s) {
-  return dispatch(w, vals, batch, true, s);
+  return dispatch(w, vals, batch, s);
 }
 
 }  // namespace gs

@@ -65,7 +65,7 @@ def test_grid_equals_sort(case):
         assert np.all(err < 1e-5), dict(zip(FIELDS, err))
 
 
-@pytest.mark.parametrize("tile,batch", [(8, 32), (8, 64), (16, 64), (32, 32), (32, 128)])
+@pytest.mark.parametrize("tile,batch", [(8, 32), (8, 64), (16, 64), (32, 64), (32, 128)])
 def test_grid_launch_shapes(tile, batch):
     g, v = CASES["ragged"]()
     go = S.grad_out(14, v.out_h, v.out_w)

@@ -52,6 +52,9 @@ SINGLE = [
     (lambda G, V: setattr(V[0], "tile", 24), b"tile must be"),
     (lambda G, V: setattr(V[0], "batch", 16), b"batch must be"),
     (lambda G, V: setattr(V[0], "batch", 1024), b"batch must be"),
+    (lambda G, V: setattr(V[0], "batch", 128), b"batch must be"),
+    (lambda G, V: (setattr(V[0], "tile", 32), setattr(V[0], "batch", 32)), b"batch must be"),
+    (lambda G, V: (setattr(V[0], "tile", 8), setattr(V[0], "batch", 512)), b"batch must be"),
     (lambda G, V: setattr(G[0], "n", 2305), b"m * lr_h"),
     (lambda G, V: setattr(G[0], "rgb", None), b"null parameter pointer"),
 ]
@@ -83,7 +86,7 @@ def test_call_level_rules(lib):
     assert b"null" in lib.gs_last_error()
 
 
-@pytest.mark.parametrize("field,value", [("tile", 8), ("batch", 128), ("adjoint", 2),
+@pytest.mark.parametrize("field,value", [("tile", 8), ("batch", 32), ("adjoint", 2),
                                          ("binning", 1)])
 def test_batch_members_must_agree(lib, field, value):
     G, V = _request(2)

@@ -9,6 +9,9 @@ Two comparisons (GSASR's render is defined on real-valued parameters):
        that rounding the parameters to BF16 / FP16 causes. Reported as max-abs,
        normwise and PSNR; the 3e-3 bound applies to the RMS error relative to
        the image maximum (the max-norm error of BF16 storage alone is ~7e-3).
+       The adjoint's storage error is reported the same way per gradient field
+       (normwise and RMS relative to the field's largest magnitude), and the
+       same 3e-3 RMS bound applies to every field.
 """
 import numpy as np
 import pytest
@@ -51,3 +54,13 @@ def test_config4(dtype, scale, record_property):
     record_property("storage_error", stats)
     print(f"{dtype} x{scale:g}: storage error {stats}")
     assert rms_rel < 3e-3, stats
+    # the adjoint's storage error, per field, against the FP32 originals
+    ref_g32 = oracle.adjoint(g.originals, v, go)
+    gd = gr - ref_g32
+    peak = np.abs(ref_g32).max(axis=0)
+    g_stats = {f: {"normwise": float(np.abs(gd[:, k]).max() / peak[k]),
+                   "rms_rel": float(np.sqrt(np.mean(gd[:, k] ** 2)) / peak[k])}
+               for k, f in enumerate(FIELDS)}
+    record_property("adjoint_storage_error", g_stats)
+    print(f"{dtype} x{scale:g}: adjoint storage error {g_stats}")
+    assert all(e["rms_rel"] < 3e-3 for e in g_stats.values()), g_stats

@@ -57,7 +57,7 @@ def test_config2_adjoint_and_fd():
     assert np.all(err < 2e-5), dict(zip(FIELDS, err))
 
 
-@pytest.mark.parametrize("tile,batch", [(8, 32), (16, 64), (32, 32)])
+@pytest.mark.parametrize("tile,batch", [(8, 32), (16, 64), (32, 64), (32, 128)])
 def test_ragged_adjoint(tile, batch):
     g = S.draw_gaussians(3, 37, 53, 1, (0.3, 2.0))
     s = 2.7
