@@ -74,7 +74,7 @@ def measured_traffic(workload_name, kernel, args):
     key = (workload_name, kernel)
     default_flags = args.norm is None and args.align is None and args.ratio is None and \
         not args.tile and not args.batch and getattr(args, "adjoint", None) is None and \
-        getattr(args, "binning", None) is None
+        getattr(args, "binning", None) is None and getattr(args, "raster", None) is None
     if sha != TRAFFIC_SRC_SHA256 or key not in TRAFFIC or not default_flags:
         return None, None
     return TRAFFIC[key]
@@ -190,11 +190,14 @@ def apply_view_flags(views, args):
             d["window"], d["trunc_k"] = S.WINDOW_RATIO, args.ratio
         d.pop("adjoint", None)
         d.pop("binning", None)
+        d.pop("raster", None)
         nv = S.View(**d)
         if getattr(args, "adjoint", None) is not None:
             nv.adjoint = {"auto": 0, "tile": 1, "gaussian": 2}[args.adjoint]
         if getattr(args, "binning", None) is not None:
             nv.binning = {"auto": 0, "sort": 1, "grid": 2}[args.binning]
+        if getattr(args, "raster", None) is not None:
+            nv.raster = {"auto": 0, "tile": 1, "pair": 2}[args.raster]
         out.append(nv)
     return out
 
@@ -202,10 +205,36 @@ def apply_view_flags(views, args):
 # --------------------------------------------------------------------------
 # Clock sampling during the timed region
 # --------------------------------------------------------------------------
+# NVML clock sampler run as its own process (read-only queries), so that the
+# benchmark's launch loop, which holds the Python interpreter lock, cannot
+# delay the samples: one line "time sm_mhz max_mhz reason_bits" per sample.
+_NVML_LOOP = r"""
+import ctypes, sys, time
+lib = ctypes.CDLL("libnvidia-ml.so.1")
+if lib.nvmlInit_v2() != 0:
+    sys.exit(1)
+h = ctypes.c_void_p()
+bus, idx, iv = sys.argv[1].encode(), int(sys.argv[2]), float(sys.argv[3])
+if not bus or lib.nvmlDeviceGetHandleByPciBusId_v2(ctypes.c_char_p(bus), ctypes.byref(h)) != 0:
+    if lib.nvmlDeviceGetHandleByIndex_v2(idx, ctypes.byref(h)) != 0:
+        sys.exit(2)
+clk, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx))
+get = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+    lib.nvmlDeviceGetCurrentClocksThrottleReasons
+while True:
+    if lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0 and get(h, ctypes.byref(rs)) == 0:
+        sys.stdout.write(f"{time.time():.6f} {clk.value} {mx.value} {rs.value}\n")
+        sys.stdout.flush()
+    time.sleep(iv)
+"""
+
+
 class ClockSampler:
-    """SM clock, power and clock-event reasons of one GPU, sampled every 2 ms
-    from a thread through NVML (read-only queries; nvidia-smi at 200 ms if the
-    NVML library cannot be loaded) while the timed region runs."""
+    """SM clock and clock-event reasons of one GPU, sampled every 2 ms by a
+    separate process through NVML (read-only; nvidia-smi every 200 ms if that
+    fails), timestamped, from before the timed region to the end of a
+    clock-sampled repeat of it."""
     REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
                0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -215,65 +244,52 @@ class ClockSampler:
     def __init__(self, gpu_index: int, interval_s: float = 0.002):
         self.gpu = gpu_index
         self.interval = interval_s
-        self.samples = []   # (sm_mhz, max_mhz, reason bits or names)
+        self.samples = []   # (host time, sm_mhz, max_mhz, reason names)
         self.proc = None
-        self.nvml = None
-        self.handle = None
-        self._stop = threading.Event()
-        self.thread = None
+        self.src = None
+        self.t0 = self.t1 = None
+        self._first = threading.Event()
 
-    def _open_nvml(self):
-        import ctypes
-        try:
-            lib = ctypes.CDLL("libnvidia-ml.so.1")
-        except OSError:
-            return False
-        if lib.nvmlInit_v2() != 0:
-            return False
-        h = ctypes.c_void_p()
-        ok = False
+    def _bus_id(self):
         try:
             import torch
             p = torch.cuda.get_device_properties(self.gpu)
-            bus = f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0".encode()
-            ok = lib.nvmlDeviceGetHandleByPciBusId_v2(ctypes.c_char_p(bus), ctypes.byref(h)) == 0
+            return f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
         except Exception:
-            ok = False
-        if not ok and lib.nvmlDeviceGetHandleByIndex_v2(self.gpu, ctypes.byref(h)) != 0:
-            return False
-        self.nvml, self.handle = lib, h
-        return True
-
-    def _nvml_loop(self):
-        import ctypes
-        lib, h = self.nvml, self.handle
-        clk, mx, reasons = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
-        lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx))
-        get_reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
-            lib.nvmlDeviceGetCurrentClocksThrottleReasons
-        while not self._stop.is_set():
-            if lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0 and \
-                    get_reasons(h, ctypes.byref(reasons)) == 0:
-                self.samples.append((float(clk.value), float(mx.value), int(reasons.value)))
-            time.sleep(self.interval)
+            return ""
 
     def start(self):
-        if self._open_nvml():
-            self.thread = threading.Thread(target=self._nvml_loop, daemon=True)
-            self.thread.start()
-            return
+        try:
+            self.proc = subprocess.Popen(
+                [sys.executable, "-c", _NVML_LOOP, self._bus_id(), str(self.gpu), str(self.interval)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.src = f"nvml every {self.interval * 1e3:g} ms"
+            threading.Thread(target=self._read_nvml, daemon=True).start()
+            if self._first.wait(10.0):
+                return
+            self.proc.kill()
+        except Exception:
+            pass
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
                  "--format=csv,noheader,nounits", "-lms", "200"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.src = "nvidia-smi every 200 ms"
+            threading.Thread(target=self._read_smi, daemon=True).start()
         except Exception:
             self.proc = None
-            return
-        self.thread = threading.Thread(target=self._smi_loop, daemon=True)
-        self.thread.start()
 
-    def _smi_loop(self):
+    def _read_nvml(self):
+        for line in self.proc.stdout:
+            parts = line.split()
+            if len(parts) == 4:
+                bits = int(parts[3])
+                self.samples.append((float(parts[0]), float(parts[1]), float(parts[2]),
+                                     {n for b, n in self.REASONS.items() if bits & b}))
+                self._first.set()
+
+    def _read_smi(self):
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
         for line in self.proc.stdout:
             parts = [p.strip() for p in line.split(",")]
@@ -282,35 +298,38 @@ class ClockSampler:
                     sm, mx = float(parts[1]), float(parts[2])
                 except ValueError:
                     continue
-                self.samples.append((sm, mx, {n for n, v in zip(names, parts[5:9])
-                                              if "Active" in v and "Not" not in v}))
+                self.samples.append((time.time(), sm, mx, {n for n, v in zip(names, parts[5:9])
+                                                           if "Active" in v and "Not" not in v}))
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
 
     def stop(self):
-        if self.nvml is not None:
-            self._stop.set()
-            self.thread.join(timeout=5)
-            src = f"nvml every {self.interval * 1e3:g} ms"
-        elif self.proc is not None:
-            time.sleep(0.25)
-            self.proc.terminate()
-            try:
-                self.proc.wait(timeout=5)
-            except Exception:
-                self.proc.kill()
-            src = "nvidia-smi every 200 ms"
-        else:
+        if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock sampling unavailable"]}
-        sm = [s[0] for s in self.samples]
-        mx = [s[1] for s in self.samples]
+        time.sleep(max(0.01, 2 * self.interval))
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        t0 = self.t0 if self.t0 is not None else float("-inf")
+        t1 = self.t1 if self.t1 is not None else float("inf")
+        load = [x for x in self.samples if x[0] >= t0]   # the timed region and the repeat after it
+        timed = [x for x in load if x[0] <= t1]
+        sm = [x[1] for x in load]
         reasons = set()
-        for s in self.samples:
-            if isinstance(s[2], set):
-                reasons |= s[2]
-            else:
-                reasons |= {n for b, n in self.REASONS.items() if s[2] & b}
+        for x in load:
+            reasons |= x[3]
         return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
-                "samples": len(self.samples), "source": src}
+                "sm_max_mhz": max(x[2] for x in load) if load else None,
+                "reasons": sorted(reasons), "samples": len(load),
+                "samples_timed_region": len(timed),
+                "sm_mhz_timed_region": statistics.median([x[1] for x in timed]) if timed else None,
+                "source": self.src}
 
 
 # --------------------------------------------------------------------------
@@ -319,16 +338,17 @@ class ClockSampler:
 # Algorithmic DRAM bytes of the memory-bound passes (per launch): the footprint
 # pass reads each Gaussian's parameters and writes its 64-byte record (and, with
 # grid binning, its 8-byte compact window); the chain rule reads parameters and
-# the 48 bytes of record-space moments and writes 36 bytes of gradients; the
-# clearing writes the moments; with sorted binning the emit pass writes 8 bytes
+# the 32 bytes of record-space moments and writes 36 bytes of gradients and
+# the 32 bytes of cleared moments (the footprint pass clears them too); with
+# sorted binning the emit pass writes 8 bytes
 # per (tile, Gaussian) pair (reading 16 bytes of each record), a radix histogram
 # pass reads the 4-byte keys, a scatter pass reads and writes keys and values
 # (16 bytes per pair) and the ranges pass reads the keys.
 def hbm_stage_rates(stage_raw, steps, stats, dtname, grid):
     n, pairs = stats["n_gaussians"], stats["tile_pairs"]
     pb = {"f32": 36, "bf16": 18, "f16": 18}[dtname]
-    per_launch = {"preprocess": n * (pb + 64 + (8 if grid else 0)),
-                  "preprocess_bwd": n * (pb + 48 + 36), "memset": n * 48,
+    per_launch = {"preprocess": n * (pb + 64 + 32 + (8 if grid else 0)),
+                  "preprocess_bwd": n * (pb + 32 + 36 + 32),
                   "emit": pairs * 8 + n * 16, "radix_hist": pairs * 4,
                   "radix_scatter": pairs * 16, "ranges": pairs * 4}
     peak = float(load_peaks()[0].get("hbm_gbs", 6800.0))
@@ -434,7 +454,7 @@ def run_gpu(args, rank, world, local_rank):
         tuned = T.tune(dgs, views, with_grads=with_adj, reps=3)
         args.tile, args.batch = tuned["tile"], tuned["batch"]
         for v in views:
-            v.binning = tuned["binning_code"]
+            v.binning, v.raster, v.adjoint = tuned["binning_code"], tuned["raster"], tuned["adjoint"]
     plan = gs.Plan(dgs, views, tile=args.tile, batch=args.batch, with_grads=with_adj)
     if with_adj:
         for i, v in enumerate(views):
@@ -470,6 +490,7 @@ def run_gpu(args, rank, world, local_rank):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    clocks.mark_start()
     launches0 = gs.launch_count()
     # the dominant kernel is bracketed on every `kernel_every`-th timed step
     # (by default every step; sparser: never the first, which follows the host
@@ -527,6 +548,7 @@ def run_gpu(args, rank, world, local_rank):
         launches = gs.launch_count() - launches0
         gs.timing_enable([])
         ktimes = gs.timing_read()
+    clocks.mark_end()
     timed_ktimes = dict(ktimes)
     if world > 1:
         dist.barrier()
@@ -540,7 +562,6 @@ def run_gpu(args, rank, world, local_rank):
             step()
         torch.cuda.synchronize()
     clk = clocks.stop()
-    clk["samples_timed_region"] = n_timed_samples
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
 
@@ -626,12 +647,16 @@ def run_gpu(args, rank, world, local_rank):
         "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}",
                    "view": view_desc(views[0]),
                    "l2": "flushed before every step (256 MiB write, outside the timed events)",
-                   "tile": plan.V[0].tile or 16, "smem_batch": plan.V[0].batch or 32,
+                   "tile": plan.V[0].tile or 16,
+                   "smem_batch": plan.V[0].batch or (64 if plan.V[0].tile == 32 else 32),
                    "binning": binning_desc(plan.V[0].binning, gsets, views),
                    "autotuned": None if tuned is None else {k: tuned[k] for k in
-                                                           ("tile", "batch", "binning", "ms",
+                                                           ("tile", "batch", "binning", "raster",
+                                                            "adjoint", "ms",
                                                             "from_cache", "n_timed")},
-                   "adjoint": "gaussian-warp" if plan.V[0].adjoint == 2 else "tile",
+                   "adjoint": ("gaussian-warp" if plan.V[0].adjoint == 2 else "tile") if with_adj
+                   else None,
+                   "raster": "pair of tiles" if stats.get("raster") == 2 else "tile",
                    "cuda_graph": bool(use_graph),
                    "hr_pixels_per_step": shard_info["job_hr_pixels"],
                    "gaussians": sum(g.n for g in dgs),
@@ -1128,6 +1153,8 @@ def main():
                     help="adjoint kernel: per-tile with atomics, or one warp per Gaussian")
     ap.add_argument("--binning", choices=["auto", "sort", "grid"], default=None,
                     help="per-tile Gaussian lists: radix-sorted pairs or grid-implicit")
+    ap.add_argument("--raster", choices=["auto", "tile", "pair"], default=None,
+                    help="forward raster layout: one warp per tile or per pair of tiles")
     ap.add_argument("--tune", dest="tune", action="store_true", default=None,
                     help="pick tile / batch / binning with the library's autotuner "
                          "(default for the c3 workload)")

@@ -121,6 +121,19 @@ typedef enum { GS_ADJOINT_AUTO = 0, GS_ADJOINT_TILE = 1, GS_ADJOINT_GAUSSIAN = 2
  * the forward is bitwise the same. */
 typedef enum { GS_BINNING_AUTO = 0, GS_BINNING_SORT = 1, GS_BINNING_GRID = 2 } gs_binning;
 
+/* How the forward raster lays its warps over the screen tiles (a launch
+ * parameter: the image is the same bit for bit):
+ *   TILE: one warp per tile (tile 16: each thread one column, eight rows);
+ *   PAIR: one warp per horizontal pair of 16 x 16 tiles, each thread one
+ *         column of each tile: the per-Gaussian work (shared-memory staging,
+ *         operand loads) is shared by the two tiles, and each tile is computed
+ *         only for the Gaussians whose window meets it. Needs GRID binning and
+ *         tile 16 (GS_ERR_UNSUPPORTED otherwise);
+ *   AUTO: PAIR with GRID binning at tile 16 when every view uses the SIGMA
+ *         window and some view's scale is >= 6 (large windows, where it
+ *         measured faster), else TILE. */
+typedef enum { GS_RASTER_AUTO = 0, GS_RASTER_TILE = 1, GS_RASTER_PAIR = 2 } gs_raster;
+
 /* The Gaussian primary head's activations (Sec. 3.2, "Gaussian Primary Head"),
  * fused into the render: with a head the five arrays of gs_gaussians hold raw
  * head outputs, mapped per Gaussian to the physical parameters
@@ -180,6 +193,7 @@ typedef struct gs_view {
                            and the adjoints of the bands of a partition sum to the whole image's
                            (the row split of one image over several devices, one sum of the
                            gradients). */
+  int32_t raster;       /* gs_raster; every view of one batched call must agree */
 } gs_view;
 
 /* Counters of the last forward call on a workspace. */
@@ -190,6 +204,8 @@ typedef struct gs_stats {
   int64_t n_gaussians;  /* total Gaussians over all images */
   int32_t n_tiles;      /* screen tiles over all images */
   int32_t status;       /* device status word (gs_status) */
+  int32_t raster;       /* the forward raster's layout that ran (GS_RASTER_TILE or _PAIR) */
+  int32_t reserved;
 } gs_stats;
 
 /* Bytes of workspace for rendering n_images images (arrays of n_images entries,
@@ -338,14 +354,16 @@ typedef struct gs_tuning {
   float ms;                               /* median time of one call (forward + adjoint if timed) */
   int32_t from_cache;                     /* 1: read from the cache file, nothing was timed */
   int32_t n_timed;                        /* candidates timed */
-  int32_t reserved;
+  int32_t raster;                         /* value for gs_view.raster */
 } gs_tuning;
 
 /* Autotuner for the launch parameters (not part of the method: they change the
  * speed, not the result). Times the render of these images, forward and, when
  * grad_outs and grads are non-NULL, the adjoint, on `stream` for each
  * candidate: tile 16, 8 and 32 with batch 32 and 64 (64 and 128 at tile 32),
- * each with SORT binning and, where it applies, GRID binning; adjoint TILE.
+ * each with SORT binning and, where it applies, GRID binning (raster TILE), and
+ * at tile 16 GRID binning with raster PAIR; all with adjoint TILE, then, when
+ * the adjoint is timed, the fastest of these with adjoint GAUSSIAN.
  * Every candidate runs twice untimed, then `reps` times (1..100) between CUDA
  * events; the median decides. The fastest is returned in *best (host). A
  * candidate whose pairs do not fit the workspace is skipped: size `ws` with
@@ -353,13 +371,13 @@ typedef struct gs_tuning {
  * pairs). outs / grads are overwritten by the timed calls. Synchronous.
  *
  * cache_path (may be NULL): a JSON-lines file, one object per tuned workload,
- *   {"signature": "...", "tile": T, "batch": B, "binning": N, "adjoint": A, "ms": t},
+ *   {"signature": "...", "tile": T, "batch": B, "binning": N, "adjoint": A, "raster": R, "ms": t},
  * the signature being the device name, parameter dtype, fwd or fwd+bwd, and
  * the log2 size classes of the HR pixels, the images and the pairs per pixel.
  * A matching line is returned without timing (from_cache = 1); a new result is
  * appended. g, v, outs, grad_outs, grads: as for gs_render_batched /
- * gs_render_batched_bwd (the views' own tile, batch, binning and adjoint are
- * ignored). */
+ * gs_render_batched_bwd (the views' own tile, batch, binning, adjoint and
+ * raster are ignored). */
 gs_status gs_tune(int32_t n_images, const gs_gaussians* g, const gs_view* v, float* const* outs,
                   const float* const* grad_outs, float* const* grads, void* ws, size_t ws_bytes,
                   void* stream, int32_t reps, const char* cache_path, gs_tuning* best);

@@ -21,6 +21,7 @@ GS_WINDOW_SIGMA, GS_WINDOW_RATIO = 0, 1
 GS_ALIGN_EQ4, GS_ALIGN_HALF = 0, 1
 GS_ADJOINT_AUTO, GS_ADJOINT_TILE, GS_ADJOINT_GAUSSIAN = 0, 1, 2
 GS_BINNING_AUTO, GS_BINNING_SORT, GS_BINNING_GRID = 0, 1, 2
+GS_RASTER_AUTO, GS_RASTER_TILE, GS_RASTER_PAIR = 0, 1, 2
 
 EXPORTS = ("gs_workspace_size", "gs_count_pairs", "gs_render_fwd", "gs_render_bwd",
            "gs_render_batched", "gs_render_batched_bwd", "gs_sync_status", "gs_read_stats",
@@ -50,13 +51,15 @@ class GsView(ctypes.Structure):
                 ("norm", ctypes.c_int32), ("tile", ctypes.c_int32),
                 ("batch", ctypes.c_int32), ("window", ctypes.c_int32),
                 ("align", ctypes.c_int32), ("adjoint", ctypes.c_int32),
-                ("binning", ctypes.c_int32), ("row0", ctypes.c_int32)]
+                ("binning", ctypes.c_int32), ("row0", ctypes.c_int32),
+                ("raster", ctypes.c_int32)]
 
 
 class GsStats(ctypes.Structure):
     _fields_ = [("tile_pairs", ctypes.c_int64), ("pixel_pairs", ctypes.c_int64),
                 ("capacity", ctypes.c_int64), ("n_gaussians", ctypes.c_int64),
-                ("n_tiles", ctypes.c_int32), ("status", ctypes.c_int32)]
+                ("n_tiles", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("raster", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class GsPeaks(ctypes.Structure):
@@ -69,7 +72,7 @@ class GsPeaks(ctypes.Structure):
 class GsTuning(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int32), ("batch", ctypes.c_int32), ("binning", ctypes.c_int32),
                 ("adjoint", ctypes.c_int32), ("ms", ctypes.c_float), ("from_cache", ctypes.c_int32),
-                ("n_timed", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("n_timed", ctypes.c_int32), ("raster", ctypes.c_int32)]
 
 
 class GsError(RuntimeError):

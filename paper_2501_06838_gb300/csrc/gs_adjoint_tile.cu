@@ -88,38 +88,15 @@ __global__ void __launch_bounds__(32) k_raster_bwd_tile(Ws w, const uint32_t* va
   }
   __syncwarp();
 
-  // A chunk's records are copied into shared memory (cp.async) while the
-  // chunk before it is computed, and its ids are loaded one chunk earlier
-  // still, so that no global-memory latency sits in front of a chunk.
-  __shared__ __align__(16) float4 srec[32][kRecordF4];
-  auto load_id = [&](int i) { return i < n ? __ldg(vals + range.x + i) : 0xffffffffu; };
-  auto copy_record = [&](uint32_t gid) {
-    if (gid < (uint32_t)w.n) {   // the list holds Gaussian ids
+  for (int base = 0; base < n; base += 32) {
+    const int i = base + lane;
+    const uint32_t gid = i < n ? __ldg(vals + range.x + i) : 0xffffffffu;
+    const bool valid = gid < (uint32_t)w.n;   // the list holds Gaussian ids
+    float4 f[kRecordF4];
+    if (valid) {
       const float4* rec = w.records + (int64_t)gid * kRecordF4;
 #pragma unroll
-      for (int q = 0; q < kRecordF4; ++q) {
-        const unsigned dst = static_cast<unsigned>(__cvta_generic_to_shared(&srec[lane][q]));
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(rec + q) : "memory");
-      }
-    }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-  };
-  uint32_t gid_cur = load_id(lane);
-  uint32_t gid_next = load_id(32 + lane);
-  copy_record(gid_cur);
-  for (int base = 0; base < n; base += 32) {
-    const uint32_t gid = gid_cur;
-    const bool valid = gid < (uint32_t)w.n;
-    asm volatile("cp.async.wait_all;\n" ::: "memory");
-    __syncwarp();
-    float4 f[kRecordF4];
-#pragma unroll
-    for (int q = 0; q < kRecordF4; ++q) f[q] = srec[lane][q];
-    __syncwarp();
-    if (base + 32 < n) {
-      copy_record(gid_next);
-      gid_cur = gid_next;
-      gid_next = load_id(base + 64 + lane);
+      for (int q = 0; q < kRecordF4; ++q) f[q] = rec[q];
     }
     // the Gaussian's record in tile-local coordinates
     float cxl = 0.f, cyl = 0.f, sA = 0.f, sK = 0.f, gy2 = 0.f, l = 0.f, cr = 0.f, cg = 0.f, cb = 0.f;
@@ -138,10 +115,10 @@ __global__ void __launch_bounds__(32) k_raster_bwd_tile(Ws w, const uint32_t* va
     // rows some lane's window reaches
     const int rlo = __reduce_min_sync(0xffffffffu, ly0);
     const int rhi = __reduce_max_sync(0xffffffffu, ly1);
+
     const float2 cr2 = p2(cr, cr), cg2 = p2(cg, cg), cb2 = p2(cb, cb), nsK2 = p2(-sK, -sK);
     float2 Cr = p2(0.f, 0.f), Cg = Cr, Cb = Cr;
-    // moments, the two columns of a pair kept apart until the end
-    float2 Sd = p2(0.f, 0.f), SY = Sd, Sdd = Sd, SdY = Sd, SYY = Sd;
+    float Sd = 0.f, SY = 0.f, Sdd = 0.f, SdY = 0.f, SYY = 0.f;
 #pragma unroll
     for (int seg = 0; seg < TILE / SEG; ++seg) {
       // per column pair: Xs = sA X (kFarG outside the window)
@@ -184,17 +161,17 @@ __global__ void __launch_bounds__(32) k_raster_bwd_tile(Ws w, const uint32_t* va
             A2 = __ffma2_rn(Gwd, d, A2);
           }
         }
-        const float2 ty = __fmul2_rn(Y2, A0);
-        SY = __fadd2_rn(SY, ty);
-        SYY = __ffma2_rn(ty, Y2, SYY);
-        Sd = __fadd2_rn(Sd, A1);
-        SdY = __ffma2_rn(Y2, A1, SdY);
-        Sdd = __fadd2_rn(Sdd, A2);
+        const float a0 = A0.x + A0.y, a1 = A1.x + A1.y, a2 = A2.x + A2.y;
+        const float ty = Y * a0;
+        SY += ty;
+        SYY = fmaf(ty, Y, SYY);
+        Sd += a1;
+        SdY = fmaf(Y, a1, SdY);
+        Sdd += a2;
       }
     }
     if (valid) {
-      const float v[8] = {Sd.x + Sd.y, SY.x + SY.y, Sdd.x + Sdd.y, SdY.x + SdY.y, SYY.x + SYY.y,
-                          Cr.x + Cr.y, Cg.x + Cg.y, Cb.x + Cb.y};
+      const float v[8] = {Sd, SY, Sdd, SdY, SYY, Cr.x + Cr.y, Cg.x + Cg.y, Cb.x + Cb.y};
       float* acc = w.grec + (int64_t)gid * 12;
 #pragma unroll
       for (int k = 0; k < 8; ++k)

@@ -54,7 +54,7 @@ cudaEvent_t take_event() {
 const char* kKernelNames[kKNumKernels] = {
     "setup",      "preprocess",    "reserved",      "scan_top",   "radix_rowscan",
     "emit",       "radix_hist",    "radix_scatter", "ranges",     "raster_fwd",
-    "raster_bwd", "preprocess_bwd", "memset",        "raster_bwd_gw"};
+    "raster_bwd", "preprocess_bwd", "reserved12",    "raster_bwd_gw"};
 
 gs_status fail(gs_status st, const char* fmt, ...) {
   char buf[512];
@@ -125,6 +125,7 @@ struct Problem {
   int tile, batch;
   int adjoint;   // gs_adjoint resolved: 1 tile, 2 Gaussian-warp
   int grid;      // gs_binning resolved: 1 grid-implicit, 0 sorted pair list
+  int pair;      // gs_raster resolved: 1 one warp per pair of tiles, 0 per tile
 };
 
 gs_status validate(int32_t n_images, const gs_gaussians* g, const gs_view* v, Problem* P) {
@@ -137,6 +138,7 @@ gs_status validate(int32_t n_images, const gs_gaussians* g, const gs_view* v, Pr
   P->batch = batch_of(v[0]);
   P->adjoint = v[0].adjoint == GS_ADJOINT_GAUSSIAN ? GS_ADJOINT_GAUSSIAN : GS_ADJOINT_TILE;
   bool grid_ok = true;   // every image on a reference grid, coordinates fit int16
+  bool sigma_windows = true, large_scale = false;   // for the AUTO raster layout
   for (int i = 0; i < n_images; ++i) {
     const gs_gaussians& G = g[i];
     const gs_view& V = v[i];
@@ -163,6 +165,11 @@ gs_status validate(int32_t n_images, const gs_gaussians* g, const gs_view* v, Pr
     if (V.row0 < 0) return fail(GS_ERR_INVALID, "image %lld: row0 < 0", (long long)i);
     if (V.binning != v[0].binning)
       return fail(GS_ERR_INVALID, "image %lld: binning differs from image 0", (long long)i);
+    if (V.raster < 0 || V.raster > 2) return fail(GS_ERR_INVALID, "image %lld: unknown raster", (long long)i);
+    if (V.raster != v[0].raster)
+      return fail(GS_ERR_INVALID, "image %lld: raster differs from image 0", (long long)i);
+    if (V.window != GS_WINDOW_SIGMA) sigma_windows = false;
+    if (V.scale >= 6.0f) large_scale = true;
     if (G.ref_grid_m == 0 || V.out_w > 32767 || V.out_h > 32767) grid_ok = false;
     const double sh = std::floor((double)V.scale * V.lr_h) + 1.0;
     const double sw = std::floor((double)V.scale * V.lr_w) + 1.0;
@@ -204,6 +211,11 @@ gs_status validate(int32_t n_images, const gs_gaussians* g, const gs_view* v, Pr
                 "grid binning needs every image on a reference grid (ref_grid_m > 0) and outputs "
                 "of at most 32767 px a side");
   P->grid = (v[0].binning == GS_BINNING_GRID || (v[0].binning == GS_BINNING_AUTO && grid_ok)) ? 1 : 0;
+  const bool pair_ok = P->grid && P->tile == 16;
+  if (v[0].raster == GS_RASTER_PAIR && !pair_ok)
+    return fail(GS_ERR_UNSUPPORTED, "raster PAIR needs grid binning and tile 16");
+  P->pair = (v[0].raster == GS_RASTER_PAIR ||
+             (v[0].raster == GS_RASTER_AUTO && pair_ok && sigma_windows && large_scale)) ? 1 : 0;
   if (P->n >= (1LL << 31)) return fail(GS_ERR_UNSUPPORTED, "more than 2^31 - 1 Gaussians");
   if (P->tiles >= (1LL << 24)) return fail(GS_ERR_UNSUPPORTED, "more than 2^24 tiles");
   return GS_OK;
@@ -278,6 +290,15 @@ gs_status prepare(int32_t n_images, const gs_gaussians* g, const gs_view* v, voi
   w.sort_blocks = L.sort_blocks;
   w.scan_parts = L.scan_parts;
   c->passes = radix_passes(c->P.tiles);
+  // horizontal pairs of tiles (the forward's launch unit for grid binning at tile 16)
+  int64_t pairs = 0;
+  for (int i = 0; i < n_images; ++i) {
+    const int64_t tx = (v[i].out_w + c->P.tile - 1) / c->P.tile;
+    const int64_t ty = (v[i].out_h + c->P.tile - 1) / c->P.tile;
+    pairs += ty * ((tx + 1) / 2);
+  }
+  w.n_pairs = (int32_t)pairs;
+  w.pair = c->P.pair;
   return GS_OK;
 }
 
@@ -285,7 +306,7 @@ gs_status upload_images(const Call& c, const gs_gaussians* g, const gs_view* v, 
                         const float* const* grad_outs, float* const* grads, int reset,
                         cudaStream_t s) {
   int64_t gbase = 0;
-  int tbase = 0;
+  int tbase = 0, pbase = 0;
   const int tile = c.P.tile;
   for (int first = 0; first < c.P.n_images; first += kSetupChunk) {
     SetupChunk ch;
@@ -330,8 +351,10 @@ gs_status upload_images(const Call& c, const gs_gaussians* g, const gs_view* v, 
       d.tiles_x = (v[i].out_w + tile - 1) / tile;
       d.tiles_y = (v[i].out_h + tile - 1) / tile;
       d.t_base = tbase;
+      d.p_base = pbase;
       gbase += g[i].n;
       tbase += d.tiles_x * d.tiles_y;
+      pbase += d.tiles_y * ((d.tiles_x + 1) / 2);
     }
     cudaError_t e = launch_setup(ch, c.w, s);
     if (e != cudaSuccess) return cuda_fail(e, "setup");
@@ -402,9 +425,8 @@ gs_status run_backward(int32_t n_images, const gs_gaussians* g, const gs_view* v
   if (c.w.n == 0) return GS_OK;
   cudaError_t e;
   if (c.P.adjoint == GS_ADJOINT_TILE) {
-    // the tile adjoint adds into the record-space accumulators
-    e = launch_zero(c.w.grec, 48 * (size_t)c.w.n, s);
-    if (e != cudaSuccess) return cuda_fail(e, "memset");
+    // the tile adjoint adds into the record-space accumulators, which the
+    // forward's footprint pass zeroed and each chain rule clears after use
     const int fb = c.passes & 1;
     e = launch_raster_bwd_tile(c.w, c.w.grid ? c.w.vals[0] : c.w.vals[fb], s);
     if (e != cudaSuccess) return cuda_fail(e, "raster_bwd");
@@ -566,6 +588,8 @@ gs_status gs_read_stats(void* ws, void* stream, gs_stats* out) {
   out->n_gaussians = (int64_t)h.reserved[0];
   out->n_tiles = (int32_t)h.reserved[1];
   out->status = (int32_t)map_status(h.status);
+  out->raster = h.reserved[2] ? GS_RASTER_PAIR : GS_RASTER_TILE;
+  out->reserved = 0;
   return GS_OK;
 }
 

@@ -36,7 +36,8 @@ struct ImageDesc {
   // o = h_offset_scale raw (or tanh(raw) with kFlagOffsetTanh)
   float h_sigma_lo, h_sigma_span, h_rho_scale, h_offset_scale;
   int32_t row0;   // first image row of the output (a band; 0: the whole image)
-  int32_t pad_[3];
+  int32_t p_base; // grid binning, tile 16: first global index of this image's tile pairs
+  int32_t pad_[2];
 };
 // ImageDesc::flags
 constexpr int32_t kFlagPeak = 1;   // Z = 1 instead of Eq. 2's normalisation
@@ -105,6 +106,8 @@ struct Ws {
   int32_t scan_parts;         // size of `parts`
   int32_t grid;               // 1: grid-implicit binning (no pair list), 0: sorted pair list
   int32_t direct;             // 1: one image, its grad_out / grads pointers below (adjoint)
+  int32_t n_pairs;            // grid binning, tile 16: horizontal tile pairs over all images
+  int32_t pair;               // 1: the forward raster runs one warp per pair of tiles
   const float* grad_out0;     // direct: dL/dI of image 0
   float* grads0;              // direct: parameter gradients of image 0
 };
@@ -216,7 +219,6 @@ __device__ __forceinline__ unsigned long long effective_pairs(const Header* h) {
 cudaError_t launch_setup(const SetupChunk& c, const Ws& w, cudaStream_t s);
 cudaError_t launch_preprocess(const Ws& w, cudaStream_t s);
 cudaError_t launch_preprocess_bwd(const Ws& w, cudaStream_t s);
-cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t s);   // bytes: a multiple of 16
 cudaError_t launch_scan_counts(const Ws& w, cudaStream_t s);
 cudaError_t launch_emit(const Ws& w, cudaStream_t s);
 cudaError_t launch_sort(const Ws& w, int key_bits, cudaStream_t s, int* final_buf);
@@ -228,7 +230,7 @@ cudaError_t launch_raster_bwd_tile(const Ws& w, const uint32_t* lists, cudaStrea
 // Kernel ids for launch accounting / per-kernel timing.
 enum KernelId {
   kKSetup = 0, kKPreprocess, kKReserved2, kKScanTop, kKRadixRowscan, kKEmit, kKRadixHist,
-  kKRadixScatter, kKRanges, kKRasterFwd, kKRasterBwd, kKPreprocessBwd, kKMemset, kKRasterBwdGw,
+  kKRadixScatter, kKRanges, kKRasterFwd, kKRasterBwd, kKPreprocessBwd, kKReserved12, kKRasterBwdGw,
   kKNumKernels
 };
 

@@ -36,6 +36,7 @@ __global__ void k_setup(SetupChunk c, Ws w) {
     h->list_cursor = 0ull;
     h->reserved[0] = (unsigned long long)w.n;
     h->reserved[1] = (unsigned long long)w.tiles;
+    h->reserved[2] = (unsigned long long)w.pair;
   }
 }
 
@@ -247,6 +248,13 @@ __global__ void __launch_bounds__(kFootprintBlock) k_preprocess(Ws w) {
     const float l = (D.flags & kFlagPeak) == 0 ? -(kLog2TwoPi + log2f(sx) + log2f(sy) + 0.5f * log2f(Dr)) : 0.0f;
 
     float4* rec = w.records + gi * kRecordF4;
+    // the adjoint's record-space accumulators start at zero (the tile adjoint
+    // adds to them; the chain rule clears them again after reading them)
+    // (whole 48-byte rows: a warp's stores then cover whole sectors)
+    float4* acc = reinterpret_cast<float4*>(w.grec + gi * 12);
+    acc[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+    acc[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    acc[2] = make_float4(0.f, 0.f, 0.f, 0.f);
     rec[0] = make_float4(cx_hi, cx_lo, cy_hi, cy_lo);
     rec[1] = make_float4(sA, sK, gY, l);
     rec[2] = make_float4(al * cr, al * cg, al * cb, 0.0f);
@@ -439,7 +447,7 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(Ws w) {
   const float sA = r * isx;
   const float sK = rho * r * isy;
   const float gY = -0.5f * kLog2E * isy * isy;
-  const float4* gm = reinterpret_cast<const float4*>(w.grec + gi * 12);
+  float4* gm = reinterpret_cast<float4*>(w.grec + gi * 12);
   const float4 m0 = gm[0], m1 = gm[1];
   const float Sd = m0.x, SY = m0.y, Sdd = m0.z, SdY = m0.w, SYY = m1.x;
   const float Cr = m1.y, Cg = m1.z, Cb = m1.w;
@@ -461,6 +469,11 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(Ws w) {
     for (int k = 0; k < 9; ++k) gr[k] *= J[k];
   }
   for (int k = 0; k < 9; ++k) out[k] = gr[k];
+  // cleared for the next adjoint of the same forward (the tile adjoint adds);
+  // last, so that no load waits behind these stores, and whole 48-byte rows
+  gm[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+  gm[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+  gm[2] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 }  // namespace
@@ -485,25 +498,6 @@ cudaError_t launch_preprocess_bwd(const Ws& w, cudaStream_t s) {
   int blocks = (int)((w.n + 255) / 256);
   LaunchScope ls(kKPreprocessBwd, s);
   return launch_chain(k_preprocess_bwd, dim3(blocks), dim3(256), 0, s, w);
-}
-
-namespace {
-__global__ void __launch_bounds__(256) k_zero(float4* p, int64_t n4) {
-  griddep_wait();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4;
-       i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-}
-}  // namespace
-
-// Zero a 16-byte-aligned buffer in the chain (a kernel, so that the launches
-// around it overlap as the rest of the chain does).
-cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t s) {
-  const int64_t n4 = (int64_t)(bytes / 16);
-  if (n4 == 0) return cudaSuccess;
-  const int blocks = (int)std::min<int64_t>(4 * 152, (n4 + 255) / 256);
-  LaunchScope ls(kKMemset, s);
-  return launch_chain(k_zero, dim3(blocks), dim3(256), 0, s, reinterpret_cast<float4*>(p), n4);
 }
 
 }  // namespace gs

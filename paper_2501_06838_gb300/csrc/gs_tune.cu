@@ -1,5 +1,5 @@
 // Autotuner of the render's launch parameters (tile edge, shared-memory batch,
-// binning), behind gs_tune in include/gs.h. Host code: it times the public
+// binning, raster layout, adjoint), behind gs_tune in include/gs.h. Host code: it times the public
 // entry points with CUDA events on the caller's workload and keeps the
 // fastest choice per workload signature in an optional JSON-lines cache.
 #include <algorithm>
@@ -19,7 +19,7 @@ void set_last_error(const char* msg);
 namespace {
 
 struct Cand {
-  int tile, batch, binning;
+  int tile, batch, binning, raster, adjoint;
 };
 
 std::string signature(int32_t n_images, const gs_gaussians* g, const gs_view* v, bool adj,
@@ -43,7 +43,8 @@ std::string signature(int32_t n_images, const gs_gaussians* g, const gs_view* v,
 }
 
 // The cache is JSON lines, one object per tuned workload:
-//   {"signature": "...", "tile": 16, "batch": 32, "binning": 2, "adjoint": 1, "ms": 0.125}
+//   {"signature": "...", "tile": 16, "batch": 32, "binning": 2, "adjoint": 1, "raster": 1,
+//    "ms": 0.125}
 // (written by cache_append; other lines are skipped).
 bool cache_lookup(const char* path, const std::string& sig, gs_tuning* out) {
   if (!path) return false;
@@ -55,8 +56,8 @@ bool cache_lookup(const char* path, const std::string& sig, gs_tuning* out) {
   while (std::fgets(line, sizeof(line), f)) {
     if (std::sscanf(line,
                     " {\"signature\": \"%255[^\"]\", \"tile\": %d, \"batch\": %d, "
-                    "\"binning\": %d, \"adjoint\": %d, \"ms\": %f}",
-                    key, &t.tile, &t.batch, &t.binning, &t.adjoint, &t.ms) == 6 &&
+                    "\"binning\": %d, \"adjoint\": %d, \"raster\": %d, \"ms\": %f}",
+                    key, &t.tile, &t.batch, &t.binning, &t.adjoint, &t.raster, &t.ms) == 7 &&
         sig == key) {
       *out = t;   // the last matching line wins
       found = true;
@@ -72,8 +73,8 @@ void cache_append(const char* path, const std::string& sig, const gs_tuning& t) 
   if (!f) return;
   std::fprintf(f,
                "{\"signature\": \"%s\", \"tile\": %d, \"batch\": %d, \"binning\": %d, "
-               "\"adjoint\": %d, \"ms\": %.6f}\n",
-               sig.c_str(), t.tile, t.batch, t.binning, t.adjoint, t.ms);
+               "\"adjoint\": %d, \"raster\": %d, \"ms\": %.6f}\n",
+               sig.c_str(), t.tile, t.batch, t.binning, t.adjoint, t.raster, t.ms);
   std::fclose(f);
 }
 
@@ -99,14 +100,15 @@ extern "C" gs_status gs_tune(int32_t n_images, const gs_gaussians* g, const gs_v
       x.tile = c.tile;
       x.batch = c.batch;
       x.binning = c.binning;
-      x.adjoint = GS_ADJOINT_TILE;
+      x.raster = c.raster;
+      x.adjoint = c.adjoint;
     }
   };
   bool grid_ok = true;
   for (int i = 0; i < n_images; ++i)
     if (g[i].ref_grid_m == 0 || v[i].out_w > 32767 || v[i].out_h > 32767) grid_ok = false;
 
-  with(Cand{16, 32, GS_BINNING_SORT});
+  with(Cand{16, 32, GS_BINNING_SORT, GS_RASTER_TILE, GS_ADJOINT_TILE});
   int64_t pairs16 = 0;
   gs_status st = gs_count_pairs(n_images, g, vv.data(), ws, ws_bytes, stream, &pairs16);
   if (st != GS_OK) return st;
@@ -121,9 +123,14 @@ extern "C" gs_status gs_tune(int32_t n_images, const gs_gaussians* g, const gs_v
   for (int tile : {16, 8, 32})
     for (int b : {1, 2}) {
       const int batch = (tile == 32 ? 64 : 32) * b;
-      cands.push_back(Cand{tile, batch, GS_BINNING_SORT});
-      if (grid_ok) cands.push_back(Cand{tile, batch, GS_BINNING_GRID});
+      cands.push_back(Cand{tile, batch, GS_BINNING_SORT, GS_RASTER_TILE, GS_ADJOINT_TILE});
+      if (grid_ok) {
+        cands.push_back(Cand{tile, batch, GS_BINNING_GRID, GS_RASTER_TILE, GS_ADJOINT_TILE});
+        if (tile == 16)
+          cands.push_back(Cand{tile, batch, GS_BINNING_GRID, GS_RASTER_PAIR, GS_ADJOINT_TILE});
+      }
     }
+  if (adj) cands.push_back(Cand{16, 32, GS_BINNING_SORT, GS_RASTER_TILE, GS_ADJOINT_GAUSSIAN});
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     if (e0) cudaEventDestroy(e0);
@@ -133,7 +140,11 @@ extern "C" gs_status gs_tune(int32_t n_images, const gs_gaussians* g, const gs_v
   gs_tuning win{};
   win.ms = INFINITY;
   int timed = 0;
-  for (const Cand& c : cands) {
+  for (size_t ci = 0; ci < cands.size(); ++ci) {
+    // after the launch layouts, the fastest of them with the other adjoint
+    if (adj && ci + 1 == cands.size() && cands.back().adjoint == GS_ADJOINT_GAUSSIAN)
+      cands.back() = Cand{win.tile, win.batch, win.binning, win.raster, GS_ADJOINT_GAUSSIAN};
+    const Cand c = cands[ci];
     with(c);
     // does the pair list fit? (tile size changes the pair count)
     int64_t need = 0;
@@ -167,7 +178,8 @@ extern "C" gs_status gs_tune(int32_t n_images, const gs_gaussians* g, const gs_v
       win.tile = c.tile;
       win.batch = c.batch;
       win.binning = c.binning;
-      win.adjoint = GS_ADJOINT_TILE;
+      win.raster = c.raster;
+      win.adjoint = c.adjoint;
       win.ms = med;
     }
   }

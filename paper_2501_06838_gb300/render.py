@@ -150,7 +150,7 @@ def _struct_v(v, tile: int = 0, batch: int = 0, adjoint: int = 0) -> _abi.GsView
                        float(getattr(v, "trunc_k", 3.0)), int(getattr(v, "norm", 0)),
                        int(tile), int(batch), int(getattr(v, "window", 0)),
                        int(getattr(v, "align", 0)), int(adjoint), int(getattr(v, "binning", 0)),
-                       int(getattr(v, "row0", 0)))
+                       int(getattr(v, "row0", 0)), int(getattr(v, "raster", 0)))
 
 
 def _arrays(gs: Sequence[Gaussians], views, tile=0, batch=0):

@@ -1,5 +1,6 @@
 """Autotuner for the launch parameters of the render (screen tile edge,
-Gaussians per shared-memory batch, binning): a thin binding of the library's
+Gaussians per shared-memory batch, binning, raster layout, adjoint kernel): a
+thin binding of the library's
 gs_tune, which times every candidate on the caller's own workload with CUDA
 events (median of `reps` calls after two warm-up calls), returns the fastest
 and keeps it in a JSON-lines cache keyed by the workload's signature (device, dtype,
@@ -24,7 +25,7 @@ def default_cache() -> str:
 
 def tune(gs, views, with_grads: bool = True, reps: int = 5, cache: str | None = None,
          stream=None) -> dict:
-    """-> {"tile", "batch", "binning", "adjoint", "ms", "from_cache", "n_timed"}
+    """-> {"tile", "batch", "binning", "adjoint", "raster", "ms", "from_cache", "n_timed"}
     for this workload (the launch parameters to put in its views)."""
     cache = cache or default_cache()
     os.makedirs(os.path.dirname(cache) or ".", exist_ok=True)
@@ -48,5 +49,6 @@ def tune(gs, views, with_grads: bool = True, reps: int = 5, cache: str | None = 
                      _stream(stream), int(reps), cache.encode(), ctypes.byref(t))
     _abi.check(st, "gs_tune")
     return {"tile": t.tile, "batch": t.batch, "binning": _BINNING.get(t.binning, t.binning),
-            "binning_code": t.binning, "adjoint": t.adjoint, "ms": float(t.ms),
+            "binning_code": t.binning, "adjoint": t.adjoint, "raster": t.raster,
+            "ms": float(t.ms),
             "from_cache": bool(t.from_cache), "n_timed": t.n_timed}

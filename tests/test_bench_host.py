@@ -15,7 +15,7 @@ import oracle
 
 
 def _args(**kw):
-    d = dict(norm=None, align=None, ratio=None, adjoint=None, binning=None)
+    d = dict(norm=None, align=None, ratio=None, adjoint=None, binning=None, raster=None)
     d.update(kw)
     return argparse.Namespace(**d)
 
@@ -58,21 +58,22 @@ def test_binning_description():
 
 def test_hbm_stage_bytes():
     stats = {"n_gaussians": 1000, "tile_pairs": 5000}
-    raw = {"preprocess": (0.002, 2), "preprocess_bwd": (0.001, 2), "memset": (0.0005, 2),
+    raw = {"preprocess": (0.002, 2), "preprocess_bwd": (0.001, 2),
            "emit": (0.001, 2), "radix_hist": (0.002, 4), "radix_scatter": (0.004, 4),
            "ranges": (0.001, 2), "raster_fwd": (1.0, 2)}
     grid = bench.hbm_stage_rates(raw, 2, stats, "f32", True)
     srt = bench.hbm_stage_rates(raw, 2, stats, "bf16", False)
     assert "raster_fwd" not in grid
-    assert grid["preprocess"]["bytes_per_launch"] == 1000 * (36 + 64 + 8)
-    assert srt["preprocess"]["bytes_per_launch"] == 1000 * (18 + 64)
-    assert grid["preprocess_bwd"]["bytes_per_launch"] == 1000 * (36 + 48 + 36)
-    assert grid["memset"]["bytes_per_launch"] == 48 * 1000
+    # parameters in, the record (and compact window) and the cleared moments out
+    assert grid["preprocess"]["bytes_per_launch"] == 1000 * (36 + 64 + 32 + 8)
+    assert srt["preprocess"]["bytes_per_launch"] == 1000 * (18 + 64 + 32)
+    # parameters and moments in, gradients and the cleared moments out
+    assert grid["preprocess_bwd"]["bytes_per_launch"] == 1000 * (36 + 32 + 36 + 32)
     assert srt["radix_scatter"]["bytes_per_launch"] == 16 * 5000
     assert srt["radix_hist"]["launches_per_step"] == 2
     # rate = bytes x launches / time
     e = grid["preprocess"]
-    assert e["achieved_gbs"] == pytest.approx(108000 * 2 / 0.002e-3 / 1e9, rel=1e-3)
+    assert e["achieved_gbs"] == pytest.approx(140000 * 2 / 0.002e-3 / 1e9, rel=1e-3)
 
 
 def test_pipeline_flops_scale_with_lr_area():

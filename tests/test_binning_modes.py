@@ -140,3 +140,67 @@ def test_grid_cuda_graph_replay():
     plan.status()
     assert torch.equal(plan.outs[0], ref_out)
     assert torch.allclose(plan.grads[0], ref_gr, rtol=1e-5, atol=1e-6 * ref_gr.abs().max().item())
+
+
+RASTER_TILE, RASTER_PAIR = 1, 2
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("batch", [0, 64])
+def test_pair_raster_equals_tile_raster(case, batch):
+    """One warp per horizontal pair of 16 x 16 tiles (grid binning) renders
+    each tile with exactly the Gaussians and arithmetic of one warp per tile:
+    the images are bit for bit the same, the per-tile lists it leaves give the
+    adjoint the oracle's gradients, and the stats report the layout that ran."""
+    import torch
+    import paper_2501_06838_gb300 as gs
+    g, v = CASES[case]()
+    go = S.grad_out(15, v.out_h, v.out_w)
+    outs = {}
+    for raster in (RASTER_TILE, RASTER_PAIR):
+        v.binning, v.raster = GRID, raster
+        dg = device_gaussians(g)
+        out, ws = gs.render(dg, v, tile=16, batch=batch, check=True)
+        assert gs.read_stats(ws)["raster"] == raster
+        gr = gs.render_bwd(dg, v, torch.from_numpy(go).cuda(), ws, tile=16, batch=batch,
+                           check=True).cpu().double().numpy()
+        outs[raster] = out.cpu().numpy()
+        err = normwise(gr, oracle.adjoint(g, v, go), axis=0)
+        assert np.all(err < 1e-5), (raster, dict(zip(FIELDS, err)))
+    assert np.array_equal(outs[RASTER_TILE], outs[RASTER_PAIR])
+
+
+def test_pair_raster_batched_bands_and_auto():
+    """Pairs over an uneven batch (odd tile columns leave a last tile alone in
+    its pair), row bands of one image, and the AUTO choice (pairs only for
+    3-sigma windows at scale >= 6)."""
+    import paper_2501_06838_gb300 as gs
+    gsets, views = [], []
+    for i, (h, w, s) in enumerate([(20, 26, 2.7), (17, 23, 6.5), (9, 31, 12.0), (5, 5, 11.0)]):
+        gsets.append(S.draw_gaussians(90 + i, h, w, 1, (0.3, 2.0)))
+        views.append(S.View(h, w, S.out_size(h, s), S.out_size(w, s), s))
+    dgs = [device_gaussians(g) for g in gsets]
+    res = {}
+    for raster in (RASTER_TILE, RASTER_PAIR, 0):
+        for v in views:
+            v.binning, v.raster = GRID, raster
+        o, ws = gs.render_batched(dgs, views, check=True)
+        res[raster] = ([x.cpu().numpy() for x in o], gs.read_stats(ws)["raster"])
+    assert res[0][1] == RASTER_PAIR   # a scale >= 6 with 3-sigma windows
+    for a, b, c in zip(res[RASTER_TILE][0], res[RASTER_PAIR][0], res[0][0]):
+        assert np.array_equal(a, b) and np.array_equal(a, c)
+    for x, g, v in zip(res[RASTER_PAIR][0], gsets, views):
+        assert np.all(normwise(x.astype(np.float64), oracle.render(g, v), axis=(1, 2)) < 1e-5)
+    # a band of one image, rows 32 .. 79, against the whole image's rows
+    g, v = gsets[2], views[2]
+    v.raster = RASTER_PAIR
+    whole, _ = gs.render(dgs[2], v, check=True)
+    band = S.View(v.lr_h, v.lr_w, 48, v.out_w, v.scale)
+    band.row0, band.binning, band.raster = 32, GRID, RASTER_PAIR
+    ob, _ = gs.render(dgs[2], band, check=True)
+    assert np.array_equal(ob.cpu().numpy(), whole.cpu().numpy()[:, 32:80])
+    # AUTO keeps one warp per tile at small scales
+    v0 = views[0]
+    v0.raster = 0
+    _, ws = gs.render(dgs[0], v0, check=True)
+    assert gs.read_stats(ws)["raster"] == RASTER_TILE

@@ -55,6 +55,10 @@ SINGLE = [
     (lambda G, V: setattr(V[0], "batch", 128), b"batch must be"),
     (lambda G, V: (setattr(V[0], "tile", 32), setattr(V[0], "batch", 32)), b"batch must be"),
     (lambda G, V: (setattr(V[0], "tile", 8), setattr(V[0], "batch", 512)), b"batch must be"),
+    (lambda G, V: setattr(V[0], "raster", 3), b"unknown raster"),
+    (lambda G, V: (setattr(V[0], "raster", 2), setattr(V[0], "binning", 1)), b"raster PAIR needs"),
+    (lambda G, V: (setattr(V[0], "raster", 2), setattr(V[0], "tile", 8),
+                   setattr(V[0], "batch", 0)), b"raster PAIR needs"),
     (lambda G, V: setattr(G[0], "n", 2305), b"m * lr_h"),
     (lambda G, V: setattr(G[0], "rgb", None), b"null parameter pointer"),
 ]
@@ -87,7 +91,7 @@ def test_call_level_rules(lib):
 
 
 @pytest.mark.parametrize("field,value", [("tile", 8), ("batch", 32), ("adjoint", 2),
-                                         ("binning", 1)])
+                                         ("binning", 1), ("raster", 1)])
 def test_batch_members_must_agree(lib, field, value):
     G, V = _request(2)
     assert lib.gs_workspace_size(2, G, V, 0) > 0

@@ -111,3 +111,21 @@ def test_adjoint_entry_points_agree():
     # the adjoint sums tile contributions with atomics, in run-dependent order
     assert torch.equal(out1, out2)
     torch.testing.assert_close(gr1, gr2, rtol=1e-5, atol=1e-6 * gr2.abs().max().item())
+
+
+@pytest.mark.parametrize("adjoint", [1, 2])
+def test_repeated_adjoint_of_one_forward(adjoint):
+    """Two adjoints of one forward (e.g. a second backward through a retained
+    graph) with different upstream gradients: each equals the oracle's, so the
+    record-space accumulators start from zero every time."""
+    import torch
+    import paper_2501_06838_gb300 as gs
+    g = S.draw_gaussians(9, 37, 53, 1, (0.3, 2.0))
+    v = S.View(37, 53, S.out_size(37, 2.7), S.out_size(53, 2.7), 2.7)
+    v.adjoint = adjoint
+    dg = device_gaussians(g)
+    _, ws = gs.render(dg, v, check=True)
+    for seed in (11, 12, 11):
+        go = S.grad_out(seed, v.out_h, v.out_w)
+        gr = gs.render_bwd(dg, v, torch.from_numpy(go).cuda(), ws, check=True)
+        check(gr.cpu().double().numpy(), oracle.adjoint(g, v, go))

@@ -17,7 +17,10 @@ def test_tune_picks_and_caches(tmp_path):
     cache = str(tmp_path / "tune.jsonl")
     e1 = tune(dgs, views, with_grads=True, reps=3, cache=cache)
     assert e1["tile"] in (8, 16, 32) and e1["binning"] in ("sort", "grid")
-    assert not e1["from_cache"] and e1["n_timed"] == 12 and e1["ms"] > 0
+    assert e1["raster"] in (1, 2) and e1["adjoint"] in (1, 2)
+    # 6 launch shapes x 2 binnings, 2 pair-of-tiles layouts, then the winner
+    # with the Gaussian-warp adjoint
+    assert not e1["from_cache"] and e1["n_timed"] == 15 and e1["ms"] > 0
     import json
     with open(cache) as f:
         lines = f.read().splitlines()
@@ -26,14 +29,15 @@ def test_tune_picks_and_caches(tmp_path):
     assert (rec["tile"], rec["batch"]) == (e1["tile"], e1["batch"]) and rec["ms"] > 0
     assert rec["signature"].count("|") >= 5
     e2 = tune(dgs, views, with_grads=True, reps=3, cache=cache)
-    assert e2["from_cache"] and (e2["tile"], e2["batch"], e2["binning"]) == \
-        (e1["tile"], e1["batch"], e1["binning"])
+    assert e2["from_cache"] and (e2["tile"], e2["batch"], e2["binning"], e2["raster"],
+                                 e2["adjoint"]) == \
+        (e1["tile"], e1["batch"], e1["binning"], e1["raster"], e1["adjoint"])
     # the tuned launch renders the same image as the default one
     for v in views:
-        v.binning = e1["binning_code"]
+        v.binning, v.raster = e1["binning_code"], e1["raster"]
     out_t, _ = gs.render_batched(dgs, views, tile=e1["tile"], batch=e1["batch"], check=True)
     for v in views:
-        v.binning = 0
+        v.binning, v.raster = 0, 0
     out_d, _ = gs.render_batched(dgs, views, check=True)
     for a, b in zip(out_t, out_d):
         assert torch.allclose(a, b, rtol=1e-5, atol=1e-6 * float(b.abs().max()))
