@@ -55,29 +55,38 @@ WARP_ISSUE_PER_SM_CLK = 4
 PAIR_CYCLES = {"raster_fwd": 6.5, "raster_bwd": 12.0, "raster_bwd_gw": 12.0}
 
 # DRAM bytes (read + write) of one launch of the dominant kernel, from one ncu
-# capture per workload (summaries under profiles/), valid only for the raster
-# source they were taken on: reported as null once gs_raster.cu changes.
-TRAFFIC_SRC_SHA256 = "2f73061372f2f4ffe6fa8129874a30abb99528d14d6ff8309b6b817d75a10210"
-TRAFFIC = {("c2", "raster_bwd"): (21317120 + 0, "profiles/raster_bwd_c2_1024x1024.md"),
-           ("c4x12-bf16", "raster_bwd"): (346431744 + 23523328,
-                                          "profiles/raster_bwd_c4x12_bf16_5760x3240.md"),
-           ("c4x12-bf16", "raster_fwd"): (37893120 + 233324032,
-                                          "profiles/raster_fwd_c4x12_bf16_5760x3240.md")}
+# capture per workload (summaries under profiles/), valid only for the kernel
+# source they were taken on: reported as null once that source file changes.
+TRAFFIC = {
+    ("c2", "raster_bwd"): ("gs_adjoint_tile.cu",
+                           "711c87699c69f5916af654407512f460a1b06841c0b0627db9822900642a1164",
+                           21309184 + 0, "profiles/raster_bwd_c2_1024x1024.md"),
+    ("c4x12-bf16", "raster_bwd"): ("gs_adjoint_tile.cu",
+                                   "711c87699c69f5916af654407512f460a1b06841c0b0627db9822900642a1164",
+                                   346357760 + 22183168,
+                                   "profiles/raster_bwd_c4x12_bf16_5760x3240.md"),
+    ("c4x12-bf16", "raster_fwd"): ("gs_raster.cu",
+                                   "8e5973c072e374a8835ec44ec183473473dc459745ed1311265f7ef822a3b7e1",
+                                   38337792 + 233043200,
+                                   "profiles/raster_fwd_c4x12_bf16_5760x3240.md"),
+}
 
 
 def measured_traffic(workload_name, kernel, args):
     import hashlib
-    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2501_06838_gb300",
-                       "csrc", "gs_raster.cu")
-    with open(src, "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()
     key = (workload_name, kernel)
     default_flags = args.norm is None and args.align is None and args.ratio is None and \
         not args.tile and not args.batch and getattr(args, "adjoint", None) is None and \
         getattr(args, "binning", None) is None and getattr(args, "raster", None) is None
-    if sha != TRAFFIC_SRC_SHA256 or key not in TRAFFIC or not default_flags:
+    if key not in TRAFFIC or not default_flags:
         return None, None
-    return TRAFFIC[key]
+    src_name, sha_ok, nbytes, where = TRAFFIC[key]
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2501_06838_gb300",
+                       "csrc", src_name)
+    with open(src, "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest() != sha_ok:
+            return None, None
+    return nbytes, where
 
 
 def load_peaks():
@@ -193,7 +202,7 @@ def apply_view_flags(views, args):
         d.pop("raster", None)
         nv = S.View(**d)
         if getattr(args, "adjoint", None) is not None:
-            nv.adjoint = {"auto": 0, "tile": 1, "gaussian": 2}[args.adjoint]
+            nv.adjoint = {"auto": 0, "tile": 1, "gaussian": 2, "quadrant": 3}[args.adjoint]
         if getattr(args, "binning", None) is not None:
             nv.binning = {"auto": 0, "sort": 1, "grid": 2}[args.binning]
         if getattr(args, "raster", None) is not None:
@@ -654,8 +663,8 @@ def run_gpu(args, rank, world, local_rank):
                                                            ("tile", "batch", "binning", "raster",
                                                             "adjoint", "ms",
                                                             "from_cache", "n_timed")},
-                   "adjoint": ("gaussian-warp" if plan.V[0].adjoint == 2 else "tile") if with_adj
-                   else None,
+                   "adjoint": {2: "gaussian-warp", 3: "tile quadrants"}.get(stats.get("adjoint"), "tile")
+                   if with_adj else None,
                    "raster": "pair of tiles" if stats.get("raster") == 2 else "tile",
                    "cuda_graph": bool(use_graph),
                    "hr_pixels_per_step": shard_info["job_hr_pixels"],
@@ -1149,8 +1158,9 @@ def main():
                     help="pixel sampling: x/s (Eq. 4) or (x + 1/2)/s - 1/2")
     ap.add_argument("--ratio", type=float, default=None,
                     help="use Algorithm 1's ratio window with this r instead of the 3-sigma box")
-    ap.add_argument("--adjoint", choices=["auto", "tile", "gaussian"], default=None,
-                    help="adjoint kernel: per-tile with atomics, or one warp per Gaussian")
+    ap.add_argument("--adjoint", choices=["auto", "tile", "gaussian", "quadrant"], default=None,
+                    help="adjoint kernel: per-tile with atomics, per 8 x 8 quadrant of 16 x 16 "
+                         "tiles with atomics, or one warp per Gaussian")
     ap.add_argument("--binning", choices=["auto", "sort", "grid"], default=None,
                     help="per-tile Gaussian lists: radix-sorted pairs or grid-implicit")
     ap.add_argument("--raster", choices=["auto", "tile", "pair"], default=None,

@@ -99,11 +99,23 @@ typedef enum { GS_ALIGN_EQ4 = 0, GS_ALIGN_HALF = 1 } gs_align;
  *             atomics (summation order varies run to run);
  *   GAUSSIAN: one warp per Gaussian over its own window, one fixed summation
  *             order, no atomics: bitwise deterministic;
- *   AUTO:     the library's choice (currently TILE, the faster of the two on
- *             the measured workloads; GAUSSIAN re-reads grad_out once per
- *             (Gaussian, pixel) pair instead of once per (tile, pixel)).
- * Both compute the same derivative (Eq. 4 with the windows held fixed). */
-typedef enum { GS_ADJOINT_AUTO = 0, GS_ADJOINT_TILE = 1, GS_ADJOINT_GAUSSIAN = 2 } gs_adjoint;
+ *   QUADRANT: TILE over the 8 x 8 quadrants of 16 x 16 tiles: each quadrant's
+ *             warp keeps, from the tile's list, the Gaussians whose window
+ *             meets the quadrant, so small windows waste fewer pixel
+ *             evaluations at tile edges. Needs tile 16 (GS_ERR_UNSUPPORTED
+ *             otherwise);
+ *   AUTO:     QUADRANT at tile 16 when every view uses the SIGMA window with
+ *             trunc_k > 0 at scale < 6 (small windows, where it measured
+ *             faster), else TILE
+ *             (GAUSSIAN re-reads grad_out once per (Gaussian, pixel) pair
+ *             instead of once per (tile, pixel) and measured slower).
+ * All compute the same derivative (Eq. 4 with the windows held fixed). */
+typedef enum {
+  GS_ADJOINT_AUTO = 0,
+  GS_ADJOINT_TILE = 1,
+  GS_ADJOINT_GAUSSIAN = 2,
+  GS_ADJOINT_QUADRANT = 3
+} gs_adjoint;
 
 /* How each screen tile finds the Gaussians whose window meets it:
  *   SORT: every (tile, Gaussian) pair is emitted, radix-sorted by tile and cut
@@ -205,7 +217,8 @@ typedef struct gs_stats {
   int32_t n_tiles;      /* screen tiles over all images */
   int32_t status;       /* device status word (gs_status) */
   int32_t raster;       /* the forward raster's layout that ran (GS_RASTER_TILE or _PAIR) */
-  int32_t reserved;
+  int32_t adjoint;      /* the adjoint kernel an adjoint with the same views runs
+                           (GS_ADJOINT_TILE, _GAUSSIAN or _QUADRANT) */
 } gs_stats;
 
 /* Bytes of workspace for rendering n_images images (arrays of n_images entries,
@@ -363,7 +376,8 @@ typedef struct gs_tuning {
  * candidate: tile 16, 8 and 32 with batch 32 and 64 (64 and 128 at tile 32),
  * each with SORT binning and, where it applies, GRID binning (raster TILE), and
  * at tile 16 GRID binning with raster PAIR; all with adjoint TILE, then, when
- * the adjoint is timed, the fastest of these with adjoint GAUSSIAN.
+ * the adjoint is timed, the fastest of these with adjoint GAUSSIAN and (when
+ * its tile is 16) with adjoint QUADRANT.
  * Every candidate runs twice untimed, then `reps` times (1..100) between CUDA
  * events; the median decides. The fastest is returned in *best (host). A
  * candidate whose pairs do not fit the workspace is skipped: size `ws` with

@@ -19,7 +19,7 @@ GS_F32, GS_BF16, GS_F16 = 0, 1, 2
 GS_NORM_DENSITY, GS_NORM_PEAK = 0, 1
 GS_WINDOW_SIGMA, GS_WINDOW_RATIO = 0, 1
 GS_ALIGN_EQ4, GS_ALIGN_HALF = 0, 1
-GS_ADJOINT_AUTO, GS_ADJOINT_TILE, GS_ADJOINT_GAUSSIAN = 0, 1, 2
+GS_ADJOINT_AUTO, GS_ADJOINT_TILE, GS_ADJOINT_GAUSSIAN, GS_ADJOINT_QUADRANT = 0, 1, 2, 3
 GS_BINNING_AUTO, GS_BINNING_SORT, GS_BINNING_GRID = 0, 1, 2
 GS_RASTER_AUTO, GS_RASTER_TILE, GS_RASTER_PAIR = 0, 1, 2
 
@@ -59,7 +59,7 @@ class GsStats(ctypes.Structure):
     _fields_ = [("tile_pairs", ctypes.c_int64), ("pixel_pairs", ctypes.c_int64),
                 ("capacity", ctypes.c_int64), ("n_gaussians", ctypes.c_int64),
                 ("n_tiles", ctypes.c_int32), ("status", ctypes.c_int32),
-                ("raster", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("raster", ctypes.c_int32), ("adjoint", ctypes.c_int32)]
 
 
 class GsPeaks(ctypes.Structure):

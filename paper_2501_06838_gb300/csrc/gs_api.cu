@@ -123,7 +123,7 @@ struct Problem {
   int64_t n;
   int64_t tiles;
   int tile, batch;
-  int adjoint;   // gs_adjoint resolved: 1 tile, 2 Gaussian-warp
+  int adjoint;   // gs_adjoint resolved: 1 tile, 2 Gaussian-warp, 3 tile quadrants
   int grid;      // gs_binning resolved: 1 grid-implicit, 0 sorted pair list
   int pair;      // gs_raster resolved: 1 one warp per pair of tiles, 0 per tile
 };
@@ -136,9 +136,9 @@ gs_status validate(int32_t n_images, const gs_gaussians* g, const gs_view* v, Pr
   P->tiles = 0;
   P->tile = tile_of(v[0]);
   P->batch = batch_of(v[0]);
-  P->adjoint = v[0].adjoint == GS_ADJOINT_GAUSSIAN ? GS_ADJOINT_GAUSSIAN : GS_ADJOINT_TILE;
   bool grid_ok = true;   // every image on a reference grid, coordinates fit int16
-  bool sigma_windows = true, large_scale = false;   // for the AUTO raster layout
+  bool sigma_windows = true, large_scale = false;   // for the AUTO raster layout and adjoint
+  bool truncated = true;                             // every window a k-sigma box (trunc_k > 0)
   for (int i = 0; i < n_images; ++i) {
     const gs_gaussians& G = g[i];
     const gs_view& V = v[i];
@@ -158,7 +158,7 @@ gs_status validate(int32_t n_images, const gs_gaussians* g, const gs_view* v, Pr
     if (V.align != 0 && V.align != 1) return fail(GS_ERR_INVALID, "image %lld: unknown align", (long long)i);
     if (V.align == 1 && !(V.scale < 8388608.0f))
       return fail(GS_ERR_INVALID, "image %lld: half-pixel alignment needs scale < 2^23", (long long)i);
-    if (V.adjoint < 0 || V.adjoint > 2) return fail(GS_ERR_INVALID, "image %lld: unknown adjoint", (long long)i);
+    if (V.adjoint < 0 || V.adjoint > 3) return fail(GS_ERR_INVALID, "image %lld: unknown adjoint", (long long)i);
     if (V.adjoint != v[0].adjoint)
       return fail(GS_ERR_INVALID, "image %lld: adjoint differs from image 0", (long long)i);
     if (V.binning < 0 || V.binning > 2) return fail(GS_ERR_INVALID, "image %lld: unknown binning", (long long)i);
@@ -170,6 +170,7 @@ gs_status validate(int32_t n_images, const gs_gaussians* g, const gs_view* v, Pr
       return fail(GS_ERR_INVALID, "image %lld: raster differs from image 0", (long long)i);
     if (V.window != GS_WINDOW_SIGMA) sigma_windows = false;
     if (V.scale >= 6.0f) large_scale = true;
+    if (!(V.trunc_k > 0.0f)) truncated = false;
     if (G.ref_grid_m == 0 || V.out_w > 32767 || V.out_h > 32767) grid_ok = false;
     const double sh = std::floor((double)V.scale * V.lr_h) + 1.0;
     const double sw = std::floor((double)V.scale * V.lr_w) + 1.0;
@@ -216,6 +217,15 @@ gs_status validate(int32_t n_images, const gs_gaussians* g, const gs_view* v, Pr
     return fail(GS_ERR_UNSUPPORTED, "raster PAIR needs grid binning and tile 16");
   P->pair = (v[0].raster == GS_RASTER_PAIR ||
              (v[0].raster == GS_RASTER_AUTO && pair_ok && sigma_windows && large_scale)) ? 1 : 0;
+  if (v[0].adjoint == GS_ADJOINT_QUADRANT && P->tile != 16)
+    return fail(GS_ERR_UNSUPPORTED, "adjoint QUADRANT needs tile 16");
+  // AUTO: quadrants at tile 16 where every view has truncated SIGMA windows at
+  // scale < 6 (small windows, where they measured faster), else whole tiles
+  const bool quad_auto = P->tile == 16 && sigma_windows && truncated && !large_scale;
+  P->adjoint = v[0].adjoint == GS_ADJOINT_GAUSSIAN ? GS_ADJOINT_GAUSSIAN
+               : (v[0].adjoint == GS_ADJOINT_QUADRANT ||
+                  (v[0].adjoint == GS_ADJOINT_AUTO && quad_auto)) ? GS_ADJOINT_QUADRANT
+                                                                  : GS_ADJOINT_TILE;
   if (P->n >= (1LL << 31)) return fail(GS_ERR_UNSUPPORTED, "more than 2^31 - 1 Gaussians");
   if (P->tiles >= (1LL << 24)) return fail(GS_ERR_UNSUPPORTED, "more than 2^24 tiles");
   return GS_OK;
@@ -299,6 +309,7 @@ gs_status prepare(int32_t n_images, const gs_gaussians* g, const gs_view* v, voi
   }
   w.n_pairs = (int32_t)pairs;
   w.pair = c->P.pair;
+  w.adjoint = c->P.adjoint;
   return GS_OK;
 }
 
@@ -424,11 +435,12 @@ gs_status run_backward(int32_t n_images, const gs_gaussians* g, const gs_view* v
   }
   if (c.w.n == 0) return GS_OK;
   cudaError_t e;
-  if (c.P.adjoint == GS_ADJOINT_TILE) {
+  if (c.P.adjoint != GS_ADJOINT_GAUSSIAN) {
     // the tile adjoint adds into the record-space accumulators, which the
     // forward's footprint pass zeroed and each chain rule clears after use
     const int fb = c.passes & 1;
-    e = launch_raster_bwd_tile(c.w, c.w.grid ? c.w.vals[0] : c.w.vals[fb], s);
+    e = launch_raster_bwd_tile(c.w, c.w.grid ? c.w.vals[0] : c.w.vals[fb],
+                               c.P.adjoint == GS_ADJOINT_QUADRANT, s);
     if (e != cudaSuccess) return cuda_fail(e, "raster_bwd");
   } else {
     // one warp per Gaussian writes all its moments: no clearing, no atomics
@@ -461,6 +473,32 @@ const char* status_text(uint32_t bits) {
 namespace gs {
 
 void set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
+int resident_grid(const void* kernel, int threads, int64_t work) {
+  static std::mutex mu;
+  static std::vector<std::pair<std::pair<const void*, int>, int>> cache;   // (kernel, device) -> CTAs
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return (int)work; }
+  int ctas = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    for (const auto& e : cache)
+      if (e.first.first == kernel && e.first.second == dev) ctas = e.second;
+  }
+  if (ctas == 0) {
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        per_sm < 1 || sms < 1) {
+      cudaGetLastError();
+      return (int)work;
+    }
+    ctas = per_sm * sms;
+    std::lock_guard<std::mutex> lk(mu);
+    cache.push_back({{kernel, dev}, ctas});
+  }
+  return (int)(work < ctas ? work : ctas);
+}
 
 bool chain_overlap() {
   static const bool on = std::getenv("GS_NO_PDL") == nullptr;
@@ -589,7 +627,7 @@ gs_status gs_read_stats(void* ws, void* stream, gs_stats* out) {
   out->n_tiles = (int32_t)h.reserved[1];
   out->status = (int32_t)map_status(h.status);
   out->raster = h.reserved[2] ? GS_RASTER_PAIR : GS_RASTER_TILE;
-  out->reserved = 0;
+  out->adjoint = (int32_t)h.reserved[3];
   return GS_OK;
 }
 

@@ -59,8 +59,8 @@ struct Header {
   unsigned long long pairs;        // P, total (tile, Gaussian) pairs
   unsigned long long pixel_pairs;  // sum_i |R_i|
   unsigned long long capacity;
-  uint32_t work_counter;
-  uint32_t pad1;
+  uint32_t work_counter;            // next tile (or pair) for the forward raster's CTAs
+  uint32_t bwd_counter;             // next tile for the tile adjoint's CTAs
   unsigned long long list_cursor;  // grid mode: pair-list slots handed out to tiles
   unsigned long long reserved[10];
 };
@@ -108,6 +108,8 @@ struct Ws {
   int32_t direct;             // 1: one image, its grad_out / grads pointers below (adjoint)
   int32_t n_pairs;            // grid binning, tile 16: horizontal tile pairs over all images
   int32_t pair;               // 1: the forward raster runs one warp per pair of tiles
+  int32_t adjoint;            // the adjoint kernel of these views (gs_adjoint, resolved)
+  int32_t pad_;
   const float* grad_out0;     // direct: dL/dI of image 0
   float* grads0;              // direct: parameter gradients of image 0
 };
@@ -225,7 +227,10 @@ cudaError_t launch_sort(const Ws& w, int key_bits, cudaStream_t s, int* final_bu
 cudaError_t launch_ranges(const Ws& w, const uint32_t* sorted_keys, cudaStream_t s);
 cudaError_t launch_raster_fwd(const Ws& w, const uint32_t* sorted_vals, int batch, cudaStream_t s);
 cudaError_t launch_raster_bwd_gw(const Ws& w, cudaStream_t s);
-cudaError_t launch_raster_bwd_tile(const Ws& w, const uint32_t* lists, cudaStream_t s);
+// quadrants: walk the 8 x 8 quadrants of 16 x 16 tiles (tile 16 only), each
+// with the Gaussians of the tile's list whose window meets it
+cudaError_t launch_raster_bwd_tile(const Ws& w, const uint32_t* lists, bool quadrants,
+                                   cudaStream_t s);
 
 // Kernel ids for launch accounting / per-kernel timing.
 enum KernelId {
@@ -255,6 +260,11 @@ __device__ __forceinline__ void griddep_release() {
 }
 
 bool chain_overlap();   // false when the environment sets GS_NO_PDL (launch-mode comparisons)
+
+// CTAs of `kernel` (blocks of `threads`) that are resident on the current
+// device at once, at most `work`: the grid of a persistent launch whose CTAs
+// take their tiles from a counter. `work` when the occupancy query fails.
+int resident_grid(const void* kernel, int threads, int64_t work);
 
 // Launch one kernel of a chain with programmatic stream serialization.
 template <typename... P, typename... A>

@@ -33,10 +33,12 @@ __global__ void k_setup(SetupChunk c, Ws w) {
     h->pixel_pairs = 0ull;
     h->capacity = (unsigned long long)w.capacity;
     h->work_counter = 0u;
+    h->bwd_counter = 0u;
     h->list_cursor = 0ull;
     h->reserved[0] = (unsigned long long)w.n;
     h->reserved[1] = (unsigned long long)w.tiles;
     h->reserved[2] = (unsigned long long)w.pair;
+    h->reserved[3] = (unsigned long long)w.adjoint;
   }
 }
 
@@ -422,6 +424,7 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(Ws w) {
   griddep_release();
   griddep_wait();
   const int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gi == 0) w.hdr->bwd_counter = 0u;   // the next adjoint of this forward starts at tile 0
   if (gi >= w.n) return;
   const int im = image_of_gaussian(w.images, w.n_images, gi);
   const ImageDesc& D = w.images[im];

@@ -130,7 +130,12 @@ extern "C" gs_status gs_tune(int32_t n_images, const gs_gaussians* g, const gs_v
           cands.push_back(Cand{tile, batch, GS_BINNING_GRID, GS_RASTER_PAIR, GS_ADJOINT_TILE});
       }
     }
-  if (adj) cands.push_back(Cand{16, 32, GS_BINNING_SORT, GS_RASTER_TILE, GS_ADJOINT_GAUSSIAN});
+  // then the fastest launch layout with each other adjoint (QUADRANT at tile 16 only)
+  const size_t n_layouts = cands.size();
+  if (adj) {
+    cands.push_back(Cand{16, 32, GS_BINNING_SORT, GS_RASTER_TILE, GS_ADJOINT_GAUSSIAN});
+    cands.push_back(Cand{16, 32, GS_BINNING_SORT, GS_RASTER_TILE, GS_ADJOINT_QUADRANT});
+  }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     if (e0) cudaEventDestroy(e0);
@@ -140,10 +145,14 @@ extern "C" gs_status gs_tune(int32_t n_images, const gs_gaussians* g, const gs_v
   gs_tuning win{};
   win.ms = INFINITY;
   int timed = 0;
+  gs_tuning lay{};   // the fastest launch layout (adjoint TILE)
   for (size_t ci = 0; ci < cands.size(); ++ci) {
-    // after the launch layouts, the fastest of them with the other adjoint
-    if (adj && ci + 1 == cands.size() && cands.back().adjoint == GS_ADJOINT_GAUSSIAN)
-      cands.back() = Cand{win.tile, win.batch, win.binning, win.raster, GS_ADJOINT_GAUSSIAN};
+    if (ci == n_layouts) lay = win;
+    if (ci >= n_layouts) {
+      if (timed == 0) break;   // no layout ran
+      cands[ci] = Cand{lay.tile, lay.batch, lay.binning, lay.raster, cands[ci].adjoint};
+      if (cands[ci].adjoint == GS_ADJOINT_QUADRANT && lay.tile != 16) continue;
+    }
     const Cand c = cands[ci];
     with(c);
     // does the pair list fit? (tile size changes the pair count)

@@ -1,11 +1,14 @@
-"""The two adjoint kernels against the FP64 oracle and each other.
+"""The three adjoint kernels against the FP64 oracle and each other.
 
 TILE sums each Gaussian's moments per screen tile and adds them with atomics;
-GAUSSIAN gives each Gaussian one warp that walks its own window (Eq. 4's sum
-over R_i) in a fixed order, so its gradients are bitwise reproducible. Both
-must meet the adjoint bar (1e-5 normwise per gradient field, FP32 parameters)
-on even and odd output widths (the GAUSSIAN walk loads column pairs as float2
-only when rows are 8-byte aligned), narrow and wide windows, and batches.
+QUADRANT does the same per 8 x 8 quadrant of 16 x 16 tiles, each quadrant
+keeping the Gaussians of its tile's list whose window meets it; GAUSSIAN gives
+each Gaussian one warp that walks its own window (Eq. 4's sum over R_i) in a
+fixed order, so its gradients are bitwise reproducible. All must meet the
+adjoint bar (1e-5 normwise per gradient field, FP32 parameters) on even and
+odd output widths (the GAUSSIAN walk loads column pairs as float2 only when
+rows are 8-byte aligned; quadrants past the right and bottom edges), narrow
+and wide windows, and batches.
 """
 import numpy as np
 import pytest
@@ -17,7 +20,7 @@ from _util import absolute, device_gaussians, normwise
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
 FIELDS = ("o_x", "o_y", "sigma_x", "sigma_y", "rho", "r", "g", "b", "alpha")
-TILE, GAUSSIAN = 1, 2
+TILE, GAUSSIAN, QUADRANT = 1, 2, 3
 
 
 def _grads(g, v, go, mode, tile=0):
@@ -52,16 +55,18 @@ CASES = {
 
 
 @pytest.mark.parametrize("case", sorted(CASES))
-@pytest.mark.parametrize("mode", [TILE, GAUSSIAN])
+@pytest.mark.parametrize("mode", [TILE, GAUSSIAN, QUADRANT])
 def test_modes_vs_oracle(case, mode):
     g, v = CASES[case]()
     go = S.grad_out(11, v.out_h, v.out_w)
     _check(_grads(g, v, go, mode), oracle.adjoint(g, v, go))
 
 
-def test_gaussian_mode_off_image_and_tiny_windows():
+@pytest.mark.parametrize("mode", [GAUSSIAN, QUADRANT])
+def test_off_image_and_tiny_windows(mode):
     """Absolute centres partly or wholly outside the image, sigmas down to 0.05
-    LR px (one- and two-pixel windows: the narrowest lane layouts)."""
+    LR px (one- and two-pixel windows: the narrowest lane layouts; 50 rows
+    leave the bottom quadrants of the last tile row past the output)."""
     rng = np.random.default_rng(19)
     n = 600
     mu = np.stack([rng.uniform(-6, 36, n), rng.uniform(-6, 26, n)], 1)
@@ -71,7 +76,7 @@ def test_gaussian_mode_off_image_and_tiny_windows():
     for W in (75, 76):
         v = S.View(20, 30, 50, W, 2.5)
         go = S.grad_out(12, v.out_h, v.out_w)
-        _check(_grads(g, v, go, GAUSSIAN), oracle.adjoint(g, v, go))
+        _check(_grads(g, v, go, mode), oracle.adjoint(g, v, go))
 
 
 def test_gaussian_mode_bitwise_deterministic_and_tile_close():
@@ -82,19 +87,22 @@ def test_gaussian_mode_bitwise_deterministic_and_tile_close():
     b = _grads(g, v, go, GAUSSIAN)
     assert np.array_equal(a, b)
     t = _grads(g, v, go, TILE)
+    q = _grads(g, v, go, QUADRANT)
     ref = oracle.adjoint(g, v, go)
     _check(a, ref)
     _check(t, ref)
+    _check(q, ref)
 
 
-def test_gaussian_mode_batched_mixed_widths():
+@pytest.mark.parametrize("mode", [GAUSSIAN, QUADRANT])
+def test_batched_mixed_widths(mode):
     import torch
     import paper_2501_06838_gb300 as gs
     gsets, views = [], []
     for i, (h, w, s) in enumerate([(20, 26, 2.7), (17, 23, 3.1), (24, 16, 1.5), (9, 31, 6.25)]):
         gsets.append(S.draw_gaussians(60 + i, h, w, 1, (0.3, 2.0)))
         v = S.View(h, w, S.out_size(h, s), S.out_size(w, s), s)
-        v.adjoint = GAUSSIAN
+        v.adjoint = mode
         views.append(v)
     dgs = [device_gaussians(g) for g in gsets]
     outs, ws = gs.render_batched(dgs, views, check=True)
@@ -115,3 +123,29 @@ def test_mixed_adjoint_modes_rejected():
     with pytest.raises(_abi.GsError) as e:
         gs.render_batched([dg, dg], [v1, v2], check=True)
     assert e.value.status == _abi.GS_ERR_INVALID
+
+
+@pytest.mark.parametrize("tile", [8, 32])
+def test_quadrant_needs_tile16(tile):
+    import paper_2501_06838_gb300 as gs
+    from paper_2501_06838_gb300 import _abi
+    g = S.draw_gaussians(1, 8, 8, 1, (0.3, 2.0))
+    v = S.View(8, 8, 16, 16, 2.0)
+    v.adjoint = QUADRANT
+    with pytest.raises(_abi.GsError, match="QUADRANT needs tile 16"):
+        gs.render(device_gaussians(g), v, tile=tile, check=True)
+
+
+def test_quadrant_long_lists_partial_hits():
+    """Tiles whose lists run to hundreds of Gaussians, of which each quadrant
+    keeps a varying part (the queue refills across many list chunks), and
+    the resolved adjoint the forward reports."""
+    import paper_2501_06838_gb300 as gs
+    g = S.draw_gaussians(23, 24, 30, 4, (0.2, 3.0))
+    v = S.View(24, 30, S.out_size(24, 6.5), S.out_size(30, 6.5), 6.5)
+    go = S.grad_out(24, v.out_h, v.out_w)
+    _check(_grads(g, v, go, QUADRANT), oracle.adjoint(g, v, go))
+    v.adjoint = QUADRANT
+    _, ws = gs.render(device_gaussians(g), v, check=True)
+    st = gs.read_stats(ws)
+    assert st["adjoint"] == QUADRANT and st["tile_pairs"] > 64 * st["n_tiles"]

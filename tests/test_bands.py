@@ -143,7 +143,7 @@ def _render(g, v, go, binning=0, adjoint=0, row0=0, rows=None):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("case", sorted(CASES))
-@pytest.mark.parametrize("binning,adjoint", [(1, 1), (2, 1), (2, 2)])
+@pytest.mark.parametrize("binning,adjoint", [(1, 1), (2, 1), (2, 2), (1, 3), (2, 3)])
 def test_bands_equal_whole_image(case, binning, adjoint):
     g, v = CASES[case]()
     go = S.grad_out(46, v.out_h, v.out_w)

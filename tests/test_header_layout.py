@@ -19,8 +19,8 @@ STRUCTS = {"gs_head": _abi.GsHead, "gs_gaussians": _abi.GsGaussians, "gs_view": 
 ENUMS = ["GS_OK", "GS_ERR_INVALID", "GS_ERR_CAPACITY", "GS_ERR_CUDA", "GS_ERR_UNSUPPORTED",
          "GS_ERR_TIMEOUT", "GS_ERR_INTERNAL", "GS_F32", "GS_BF16", "GS_F16", "GS_NORM_DENSITY",
          "GS_NORM_PEAK", "GS_WINDOW_SIGMA", "GS_WINDOW_RATIO", "GS_ALIGN_EQ4", "GS_ALIGN_HALF",
-         "GS_ADJOINT_AUTO", "GS_ADJOINT_TILE", "GS_ADJOINT_GAUSSIAN", "GS_BINNING_AUTO",
-         "GS_BINNING_SORT", "GS_BINNING_GRID"]
+         "GS_ADJOINT_AUTO", "GS_ADJOINT_TILE", "GS_ADJOINT_GAUSSIAN", "GS_ADJOINT_QUADRANT",
+         "GS_BINNING_AUTO", "GS_BINNING_SORT", "GS_BINNING_GRID"]
 
 
 def _program() -> str:

@@ -45,7 +45,12 @@ SINGLE = [
     (lambda G, V: setattr(V[0], "norm", 2), b"unknown norm"),
     (lambda G, V: setattr(V[0], "window", 2), b"unknown window"),
     (lambda G, V: setattr(V[0], "align", 2), b"unknown align"),
-    (lambda G, V: setattr(V[0], "adjoint", 3), b"unknown adjoint"),
+    (lambda G, V: setattr(V[0], "adjoint", 4), b"unknown adjoint"),
+    (lambda G, V: setattr(V[0], "adjoint", -1), b"unknown adjoint"),
+    (lambda G, V: (setattr(V[0], "adjoint", 3), setattr(V[0], "tile", 8),
+                   setattr(V[0], "batch", 0)), b"adjoint QUADRANT needs tile 16"),
+    (lambda G, V: (setattr(V[0], "adjoint", 3), setattr(V[0], "tile", 32),
+                   setattr(V[0], "batch", 0)), b"adjoint QUADRANT needs tile 16"),
     (lambda G, V: setattr(V[0], "binning", 3), b"unknown binning"),
     (lambda G, V: setattr(V[0], "row0", -4), b"row0"),
     (lambda G, V: setattr(V[0], "out_w", 194), b"larger than"),

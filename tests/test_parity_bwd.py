@@ -113,7 +113,7 @@ def test_adjoint_entry_points_agree():
     torch.testing.assert_close(gr1, gr2, rtol=1e-5, atol=1e-6 * gr2.abs().max().item())
 
 
-@pytest.mark.parametrize("adjoint", [1, 2])
+@pytest.mark.parametrize("adjoint", [1, 2, 3])
 def test_repeated_adjoint_of_one_forward(adjoint):
     """Two adjoints of one forward (e.g. a second backward through a retained
     graph) with different upstream gradients: each equals the oracle's, so the
