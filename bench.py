@@ -59,15 +59,15 @@ PAIR_CYCLES = {"raster_fwd": 6.5, "raster_bwd": 12.0, "raster_bwd_gw": 12.0}
 # source they were taken on: reported as null once that source file changes.
 TRAFFIC = {
     ("c2", "raster_bwd"): ("gs_adjoint_tile.cu",
-                           "711c87699c69f5916af654407512f460a1b06841c0b0627db9822900642a1164",
-                           21309184 + 0, "profiles/raster_bwd_c2_1024x1024.md"),
+                           "24cd06189cfda294e49d6437e95ad8e287bf4cb7a68c5b3f5ef50fc5f0b082d4",
+                           21309440 + 0, "profiles/raster_bwd_c2_1024x1024.md"),
     ("c4x12-bf16", "raster_bwd"): ("gs_adjoint_tile.cu",
-                                   "711c87699c69f5916af654407512f460a1b06841c0b0627db9822900642a1164",
-                                   346357760 + 22183168,
+                                   "24cd06189cfda294e49d6437e95ad8e287bf4cb7a68c5b3f5ef50fc5f0b082d4",
+                                   350465536 + 20317440,
                                    "profiles/raster_bwd_c4x12_bf16_5760x3240.md"),
     ("c4x12-bf16", "raster_fwd"): ("gs_raster.cu",
                                    "8e5973c072e374a8835ec44ec183473473dc459745ed1311265f7ef822a3b7e1",
-                                   38337792 + 233043200,
+                                   38078464 + 233108224,
                                    "profiles/raster_fwd_c4x12_bf16_5760x3240.md"),
 }
 
