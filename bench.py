@@ -1075,8 +1075,6 @@ def run_cpu_baseline(gsets, views, with_adj, plan, seconds):
         t += time.time() - t1
         px += npx
         reps += 1
-        if use_band is None and reps >= 1 and t > seconds / 2:
-            break
     sample = (f"{reps} oracle step(s) of the full workload" if use_band is None else
               f"{reps} oracle step(s) on the top {use_band} rows of every image")
     cb = {"value": round(px / t / 1e6, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
