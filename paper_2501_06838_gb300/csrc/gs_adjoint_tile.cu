@@ -243,9 +243,10 @@ __device__ __forceinline__ void bwd_one_quadrant(const Ws& w, const uint32_t* va
 // the next tile from the workspace counter (reset by the forward's setup and
 // by the chain rule after each adjoint) until the tiles run out, so that no
 // partial last wave idles SMs. The counter is asked only after a tile is done,
-// which spreads the (same-address) atomics over the launch.
+// which spreads the (same-address) atomics over the launch. Registers capped
+// at 64 for 32 resident CTAs per SM (no spills at tile 8, 16 or 32).
 template <int TILE>
-__global__ void __launch_bounds__(32) k_raster_bwd_tile(Ws w, const uint32_t* vals) {
+__global__ void __launch_bounds__(32, 32) k_raster_bwd_tile(Ws w, const uint32_t* vals) {
   griddep_release();
   griddep_wait();
   __shared__ float4 sgA[TILE * TILE / 2];

@@ -431,7 +431,9 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(Ws w) {
   const int64_t li = gi - D.g_base;
   float* out = (w.direct ? w.grads0 : D.grads) + li * 9;
   const float4* rec = w.records + gi * kRecordF4;
-  const float4 r3 = rec[3];
+  // every load that does not depend on the image table, issued together
+  float4* gm = reinterpret_cast<float4*>(w.grec + gi * 12);
+  const float4 r3 = rec[3], rc = rec[2], m0 = gm[0], m1 = gm[1];
   const bool live = __float_as_int(r3.x) <= __float_as_int(r3.y) &&
                     __float_as_int(r3.z) <= __float_as_int(r3.w);
   if (!live) {
@@ -450,11 +452,8 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(Ws w) {
   const float sA = r * isx;
   const float sK = rho * r * isy;
   const float gY = -0.5f * kLog2E * isy * isy;
-  float4* gm = reinterpret_cast<float4*>(w.grec + gi * 12);
-  const float4 m0 = gm[0], m1 = gm[1];
   const float Sd = m0.x, SY = m0.y, Sdd = m0.z, SdY = m0.w, SYY = m1.x;
   const float Cr = m1.y, Cg = m1.z, Cb = m1.w;
-  const float4 rc = rec[2];
   const float S0 = fmaf(rc.z, Cb, fmaf(rc.y, Cg, rc.x * Cr));
 
   const float two_ln2 = 2.0f * kLn2;
