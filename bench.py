@@ -59,15 +59,15 @@ PAIR_CYCLES = {"raster_fwd": 6.5, "raster_bwd": 12.0, "raster_bwd_gw": 12.0}
 # source they were taken on: reported as null once that source file changes.
 TRAFFIC = {
     ("c2", "raster_bwd"): ("gs_adjoint_tile.cu",
-                           "24cd06189cfda294e49d6437e95ad8e287bf4cb7a68c5b3f5ef50fc5f0b082d4",
-                           21309440 + 0, "profiles/raster_bwd_c2_1024x1024.md"),
+                           "d329f4b6381f0a3278e01aa6c5f2dc462ed321c7207134b08b7a6235270e4c31",
+                           21309184 + 0, "profiles/raster_bwd_c2_1024x1024.md"),
     ("c4x12-bf16", "raster_bwd"): ("gs_adjoint_tile.cu",
-                                   "24cd06189cfda294e49d6437e95ad8e287bf4cb7a68c5b3f5ef50fc5f0b082d4",
-                                   350465536 + 20317440,
+                                   "d329f4b6381f0a3278e01aa6c5f2dc462ed321c7207134b08b7a6235270e4c31",
+                                   349436928 + 20665088,
                                    "profiles/raster_bwd_c4x12_bf16_5760x3240.md"),
     ("c4x12-bf16", "raster_fwd"): ("gs_raster.cu",
                                    "8e5973c072e374a8835ec44ec183473473dc459745ed1311265f7ef822a3b7e1",
-                                   38078464 + 233108224,
+                                   38270464 + 232576000,
                                    "profiles/raster_fwd_c4x12_bf16_5760x3240.md"),
 }
 
