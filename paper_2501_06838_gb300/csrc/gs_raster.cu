@@ -559,10 +559,10 @@ __device__ __forceinline__ void fwd_pair_gaussian(float2 (&accA)[4][3], float2 (
     fwd_half(accB, o.q, o.a.y, o.d.x, o.d.y, o.d.z, fcol, c0, c1, c2);
 }
 
-// 18 resident CTAs per SM (shared memory allows 18): the cap takes it from 110
-// to 93 registers with no spills.
+// PF = 1: 18 resident CTAs per SM (shared memory allows 18); the cap takes it
+// from 110 to 93 registers with no spills. PF = 2 is held to 9 by shared memory.
 template <int PF>
-__global__ void __launch_bounds__(32, 18) k_raster_fwd_pair(Ws w) {
+__global__ void __launch_bounds__(32, PF == 1 ? 18 : 1) k_raster_fwd_pair(Ws w) {
   griddep_release();
   griddep_wait();
   constexpr int NT = 32, BATCH = NT * PF;
