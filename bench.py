@@ -66,8 +66,8 @@ TRAFFIC = {
                                    349436928 + 20665088,
                                    "profiles/raster_bwd_c4x12_bf16_5760x3240.md"),
     ("c4x12-bf16", "raster_fwd"): ("gs_raster.cu",
-                                   "8e5973c072e374a8835ec44ec183473473dc459745ed1311265f7ef822a3b7e1",
-                                   38270464 + 232576000,
+                                   "a1d3fc604d7d88dbb6ddcab89fd2d676a52d2fe9dd3e9fb2e164cfe5074db27f",
+                                   37752320 + 233056512,
                                    "profiles/raster_fwd_c4x12_bf16_5760x3240.md"),
 }
 
