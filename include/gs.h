@@ -375,9 +375,9 @@ typedef struct gs_tuning {
  * grad_outs and grads are non-NULL, the adjoint, on `stream` for each
  * candidate: tile 16, 8 and 32 with batch 32 and 64 (64 and 128 at tile 32),
  * each with SORT binning and, where it applies, GRID binning (raster TILE), and
- * at tile 16 GRID binning with raster PAIR; all with adjoint TILE, then, when
- * the adjoint is timed, the fastest of these with adjoint GAUSSIAN and (when
- * its tile is 16) with adjoint QUADRANT.
+ * at tile 16 GRID binning with raster PAIR; all with adjoint TILE and, when
+ * the adjoint is timed, those at tile 16 also with adjoint QUADRANT; then the
+ * fastest of these with adjoint GAUSSIAN.
  * Every candidate runs twice untimed, then `reps` times (1..100) between CUDA
  * events; the median decides. The fastest is returned in *best (host). A
  * candidate whose pairs do not fit the workspace is skipped: size `ws` with

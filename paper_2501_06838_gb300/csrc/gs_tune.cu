@@ -119,23 +119,26 @@ extern "C" gs_status gs_tune(int32_t n_images, const gs_gaussians* g, const gs_v
     return GS_OK;
   }
 
+  // launch layouts, each with the tile adjoint and, at tile 16, also with the
+  // quadrant adjoint (which helps where windows are small, so it competes with
+  // the smaller tiles rather than only with the winner)
   std::vector<Cand> cands;
+  auto layout = [&](int tile, int batch, int binning, int raster) {
+    cands.push_back(Cand{tile, batch, binning, raster, GS_ADJOINT_TILE});
+    if (adj && tile == 16) cands.push_back(Cand{tile, batch, binning, raster, GS_ADJOINT_QUADRANT});
+  };
   for (int tile : {16, 8, 32})
     for (int b : {1, 2}) {
       const int batch = (tile == 32 ? 64 : 32) * b;
-      cands.push_back(Cand{tile, batch, GS_BINNING_SORT, GS_RASTER_TILE, GS_ADJOINT_TILE});
+      layout(tile, batch, GS_BINNING_SORT, GS_RASTER_TILE);
       if (grid_ok) {
-        cands.push_back(Cand{tile, batch, GS_BINNING_GRID, GS_RASTER_TILE, GS_ADJOINT_TILE});
-        if (tile == 16)
-          cands.push_back(Cand{tile, batch, GS_BINNING_GRID, GS_RASTER_PAIR, GS_ADJOINT_TILE});
+        layout(tile, batch, GS_BINNING_GRID, GS_RASTER_TILE);
+        if (tile == 16) layout(tile, batch, GS_BINNING_GRID, GS_RASTER_PAIR);
       }
     }
-  // then the fastest launch layout with each other adjoint (QUADRANT at tile 16 only)
+  // then the fastest of those with the Gaussian-warp adjoint
   const size_t n_layouts = cands.size();
-  if (adj) {
-    cands.push_back(Cand{16, 32, GS_BINNING_SORT, GS_RASTER_TILE, GS_ADJOINT_GAUSSIAN});
-    cands.push_back(Cand{16, 32, GS_BINNING_SORT, GS_RASTER_TILE, GS_ADJOINT_QUADRANT});
-  }
+  if (adj) cands.push_back(Cand{16, 32, GS_BINNING_SORT, GS_RASTER_TILE, GS_ADJOINT_GAUSSIAN});
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     if (e0) cudaEventDestroy(e0);
@@ -145,13 +148,10 @@ extern "C" gs_status gs_tune(int32_t n_images, const gs_gaussians* g, const gs_v
   gs_tuning win{};
   win.ms = INFINITY;
   int timed = 0;
-  gs_tuning lay{};   // the fastest launch layout (adjoint TILE)
   for (size_t ci = 0; ci < cands.size(); ++ci) {
-    if (ci == n_layouts) lay = win;
-    if (ci >= n_layouts) {
+    if (ci >= n_layouts) {   // the fastest layout so far, with the Gaussian-warp adjoint
       if (timed == 0) break;   // no layout ran
-      cands[ci] = Cand{lay.tile, lay.batch, lay.binning, lay.raster, cands[ci].adjoint};
-      if (cands[ci].adjoint == GS_ADJOINT_QUADRANT && lay.tile != 16) continue;
+      cands[ci] = Cand{win.tile, win.batch, win.binning, win.raster, cands[ci].adjoint};
     }
     const Cand c = cands[ci];
     with(c);
