@@ -23,6 +23,9 @@
 //     column pairs per step and few lanes idle.
 // Masked columns (outside [x0, x1], or lanes past the chunk) take sA X = 1e18,
 // so d stays finite, e = -1e36 and w = +0 with no branch.
+#include <atomic>
+#include <climits>
+
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -67,14 +70,19 @@ struct GwAcc {
 // One step: the lane's column pair on table row `q` (Y, Y, R, R), loads at
 // element offset `off` (second column at `off2` when the row is not 8-byte
 // aligned).
-template <bool ALIGNED>
+// SMEM: the three planes are a staged copy in shared memory (always aligned).
+template <bool ALIGNED, bool SMEM>
 __device__ __forceinline__ void gw_pixel_pair(GwAcc& a, const float* __restrict__ g0,
                                               const float* __restrict__ g1,
                                               const float* __restrict__ g2, int64_t off,
                                               int64_t off2, const float4 q, float2 Xs, float2 nsK,
                                               float2 cr, float2 cg, float2 cb) {
   float2 gr, gg, gb;
-  if (ALIGNED) {
+  if (SMEM) {
+    gr = *reinterpret_cast<const float2*>(g0 + off);
+    gg = *reinterpret_cast<const float2*>(g1 + off);
+    gb = *reinterpret_cast<const float2*>(g2 + off);
+  } else if (ALIGNED) {
     gr = __ldg(reinterpret_cast<const float2*>(g0 + off));
     gg = __ldg(reinterpret_cast<const float2*>(g1 + off));
     gb = __ldg(reinterpret_cast<const float2*>(g2 + off));
@@ -101,10 +109,15 @@ __device__ __forceinline__ void gw_pixel_pair(GwAcc& a, const float* __restrict_
   a.C[2] = __ffma2_rn(gb, wv, a.C[2]);
 }
 
-template <bool ALIGNED>
-__device__ __forceinline__ void gw_walk(const float* __restrict__ go, int64_t plane, int W, int x0,
-                                        int x1, int y0, int y1, const float4 f0, const float4 f1,
-                                        const float4 f2, float4* rt, int lane, float (&v)[8]) {
+// The walk over the window [x0, x1] x [y0, y1] (image coordinates). Pixel
+// (x, y) of the upstream gradient sits at go[(y - oy) * W + (x - ox)] of each
+// plane: the caller's image (ox = 0, oy = row0, W the output width) or a
+// staged region (its first column ox even and W even when SMEM).
+template <bool ALIGNED, bool SMEM>
+__device__ __forceinline__ void gw_walk(const float* __restrict__ go, int64_t plane, int W, int ox,
+                                        int oy, int x0, int x1, int y0, int y1, const float4 f0,
+                                        const float4 f1, const float4 f2, float4* rt, int lane,
+                                        float (&v)[8]) {
   const float cxh = f0.x, cxl = f0.y, cyh = f0.z, cyl = f0.w;
   const float sA = f1.x, gq = f1.z, l = f1.w;
   const float2 nsK = p2(-f1.y, -f1.y);
@@ -138,19 +151,19 @@ __device__ __forceinline__ void gw_walk(const float* __restrict__ go, int64_t pl
       float2 Xs = p2(sA * X.x, sA * X.y);
       if (!live || xp < x0) Xs.x = kFarGw;
       if (!live || xp + 1 > x1) Xs.y = kFarGw;
-      const int xq = min(xp + 1, W - 1);
+      const int xl = xp - ox, xq = min(xp + 1, ox + W - 1) - ox;   // columns in go
       GwAcc a;
       a.C[0] = a.C[1] = a.C[2] = a.SY = a.SYY = a.Sd = a.Sdd = a.SdY = p2(0.f, 0.f);
       int r = lr;
       for (; r + rpi < nr; r += 2 * rpi) {
-        const int64_t ya = (int64_t)(rb + r) * W, yb = ya + (int64_t)rpi * W;
+        const int64_t ya = (int64_t)(rb + r - oy) * W, yb = ya + (int64_t)rpi * W;
         const float4 qa = rt[r], qb = rt[r + rpi];
-        gw_pixel_pair<ALIGNED>(a, g0, g1, g2, ya + xp, ya + xq, qa, Xs, nsK, cr, cg, cb);
-        gw_pixel_pair<ALIGNED>(a, g0, g1, g2, yb + xp, yb + xq, qb, Xs, nsK, cr, cg, cb);
+        gw_pixel_pair<ALIGNED, SMEM>(a, g0, g1, g2, ya + xl, ya + xq, qa, Xs, nsK, cr, cg, cb);
+        gw_pixel_pair<ALIGNED, SMEM>(a, g0, g1, g2, yb + xl, yb + xq, qb, Xs, nsK, cr, cg, cb);
       }
       if (r < nr) {
-        const int64_t ya = (int64_t)(rb + r) * W;
-        gw_pixel_pair<ALIGNED>(a, g0, g1, g2, ya + xp, ya + xq, rt[r], Xs, nsK, cr, cg, cb);
+        const int64_t ya = (int64_t)(rb + r - oy) * W;
+        gw_pixel_pair<ALIGNED, SMEM>(a, g0, g1, g2, ya + xl, ya + xq, rt[r], Xs, nsK, cr, cg, cb);
       }
       tSd = __fadd2_rn(tSd, a.Sd);
       tSdd = __fadd2_rn(tSdd, a.Sdd);
@@ -189,18 +202,152 @@ __global__ void __launch_bounds__(kGwWarps * 32) k_raster_bwd_gw(Ws w) {
     const int W = D.out_w;
     const int64_t plane = (int64_t)D.out_h * W;
     // rows are image rows; the upstream gradient holds rows row0 .. row0 + out_h - 1
-    const float* go = (w.direct ? w.grad_out0 : D.grad_out) - (int64_t)D.row0 * W;
+    const float* go = w.direct ? w.grad_out0 : D.grad_out;
     const bool aligned = (W & 1) == 0 && (reinterpret_cast<uintptr_t>(go) & 7) == 0;
     if (aligned)
-      gw_walk<true>(go, plane, W, x0, x1, y0, y1, rec[0], rec[1], rec[2], rt[wp], lane, v);
+      gw_walk<true, false>(go, plane, W, 0, D.row0, x0, x1, y0, y1, rec[0], rec[1], rec[2], rt[wp],
+                           lane, v);
     else
-      gw_walk<false>(go, plane, W, x0, x1, y0, y1, rec[0], rec[1], rec[2], rt[wp], lane, v);
+      gw_walk<false, false>(go, plane, W, 0, D.row0, x0, x1, y0, y1, rec[0], rec[1], rec[2],
+                            rt[wp], lane, v);
   }
   const float s = warp_sum8(v, lane);
   if ((lane & 3) == 0) w.grec[gi * 12 + (lane >> 2)] = s;
 }
 
+// Block form, for Gaussians on a reference grid (m > 0): one CTA per block of
+// kGbCells x kGbCells LR cells of an image. The CTA first forms the union box
+// of its Gaussians' windows and, when the box fits kGbFloats, copies the
+// upstream gradient over it into shared memory once (three planes, the first
+// column even and the width even); its warps then walk their Gaussians (the
+// k-th of the block goes to warp k % kGbWarps) exactly as the one-warp form
+// does, reading the gradient from shared memory instead of L1/L2. A block
+// whose box does not fit walks the gradient in global memory. Each Gaussian's
+// sums keep the one-warp form's order, so the moments are the same bits.
+constexpr int kGbCells = 8;
+constexpr int kGbWarps = 8;
+constexpr int kGbFloats = 24 * 1024;   // 96 KB of staged gradient at most
+
+__device__ __forceinline__ int image_of_gblock(const ImageDesc* im, int n_images, int b) {
+  int lo = 0, hi = n_images - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (im[mid].b_base <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kGbWarps * 32) k_raster_bwd_gblock(Ws w) {
+  griddep_release();
+  griddep_wait();
+  extern __shared__ float2 gstage2[];   // [3][RH][RW] floats (float2 for the alignment)
+  float* gstage = reinterpret_cast<float*>(gstage2);
+  __shared__ float4 rt[kGbWarps][kGwRows];
+  __shared__ int sbox[4];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int im = image_of_gblock(w.images, w.n_images, (int)blockIdx.x);
+  const ImageDesc& D = w.images[im];
+  const int bxs = (D.lr_w + kGbCells - 1) / kGbCells;
+  const int lb = (int)blockIdx.x - D.b_base;
+  const int by = lb / bxs, bx = lb - by * bxs;
+  const int j0 = bx * kGbCells, i0 = by * kGbCells;
+  const int cw = min(kGbCells, D.lr_w - j0), ch = min(kGbCells, D.lr_h - i0);
+  const int m = D.m;
+  const int ng = cw * ch * m;
+  // global id of the block's k-th Gaussian (cells row by row, m per cell)
+  auto gid_of = [&](int k) -> int64_t {
+    const int c = k / m, sub = k - c * m;
+    const int ci = c / cw, cj = c - ci * cw;
+    return D.g_base + ((int64_t)(i0 + ci) * D.lr_w + (j0 + cj)) * m + sub;
+  };
+
+  // the union box of the live windows
+  if (threadIdx.x == 0) {
+    sbox[0] = INT_MAX; sbox[1] = INT_MIN; sbox[2] = INT_MAX; sbox[3] = INT_MIN;
+  }
+  __syncthreads();
+  {
+    int bx0 = INT_MAX, bx1 = INT_MIN, by0 = INT_MAX, by1 = INT_MIN;
+    for (int k = threadIdx.x; k < ng; k += blockDim.x) {
+      const float4 f3 = w.records[gid_of(k) * kRecordF4 + 3];
+      const int x0 = __float_as_int(f3.x), x1 = __float_as_int(f3.y);
+      const int y0 = __float_as_int(f3.z), y1 = __float_as_int(f3.w);
+      if (x0 <= x1 && y0 <= y1) {
+        bx0 = min(bx0, x0); bx1 = max(bx1, x1); by0 = min(by0, y0); by1 = max(by1, y1);
+      }
+    }
+    bx0 = __reduce_min_sync(0xffffffffu, bx0);
+    bx1 = __reduce_max_sync(0xffffffffu, bx1);
+    by0 = __reduce_min_sync(0xffffffffu, by0);
+    by1 = __reduce_max_sync(0xffffffffu, by1);
+    if (lane == 0) {
+      atomicMin(&sbox[0], bx0); atomicMax(&sbox[1], bx1);
+      atomicMin(&sbox[2], by0); atomicMax(&sbox[3], by1);
+    }
+  }
+  __syncthreads();
+  const int rx0 = sbox[0] & ~1, rx1 = sbox[1], ry0 = sbox[2], ry1 = sbox[3];
+  const bool any = rx0 <= rx1 && ry0 <= ry1;
+  const int RW = any ? ((rx1 - rx0 + 2) & ~1) : 0, RH = any ? ry1 - ry0 + 1 : 0;
+  const int64_t rplane = (int64_t)RW * RH;
+  const bool staged = any && 3 * rplane <= kGbFloats;   // uniform over the CTA
+  const int W = D.out_w;
+  const int64_t plane = (int64_t)D.out_h * W;
+  const float* go = w.direct ? w.grad_out0 : D.grad_out;
+  if (staged) {
+    for (int64_t idx = threadIdx.x; idx < rplane; idx += blockDim.x) {
+      const int r = (int)(idx / RW), x = (int)(idx - (int64_t)r * RW);
+      const int gx = rx0 + x, gy = ry0 + r - D.row0;   // output row
+      const bool in = gx < W;                            // rows are inside the output
+      const int64_t o = in ? (int64_t)gy * W + gx : 0;
+      gstage[idx] = in ? __ldg(go + o) : 0.0f;
+      gstage[rplane + idx] = in ? __ldg(go + plane + o) : 0.0f;
+      gstage[2 * rplane + idx] = in ? __ldg(go + 2 * plane + o) : 0.0f;
+    }
+  }
+  __syncthreads();
+  const bool aligned = (W & 1) == 0 && (reinterpret_cast<uintptr_t>(go) & 7) == 0;
+  for (int k = wp; k < ng; k += kGbWarps) {
+    const int64_t gi = gid_of(k);
+    const float4* rec = w.records + gi * kRecordF4;
+    const float4 f3 = rec[3];
+    const int x0 = __float_as_int(f3.x), x1 = __float_as_int(f3.y);
+    const int y0 = __float_as_int(f3.z), y1 = __float_as_int(f3.w);
+    float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (x0 <= x1 && y0 <= y1) {   // warp-uniform
+      if (staged)
+        gw_walk<true, true>(gstage, rplane, RW, rx0, ry0, x0, x1, y0, y1, rec[0], rec[1], rec[2],
+                            rt[wp], lane, v);
+      else if (aligned)
+        gw_walk<true, false>(go, plane, W, 0, D.row0, x0, x1, y0, y1, rec[0], rec[1], rec[2],
+                             rt[wp], lane, v);
+      else
+        gw_walk<false, false>(go, plane, W, 0, D.row0, x0, x1, y0, y1, rec[0], rec[1], rec[2],
+                              rt[wp], lane, v);
+    }
+    const float sum = warp_sum8(v, lane);
+    if ((lane & 3) == 0) w.grec[gi * 12 + (lane >> 2)] = sum;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_raster_bwd_gblock(const Ws& w, cudaStream_t s) {
+  if (w.n == 0 || w.n_gblocks == 0) return cudaSuccess;
+  static std::atomic<int> configured_device{-1};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured_device.load() != dev) {
+    const cudaError_t e = cudaFuncSetAttribute(k_raster_bwd_gblock,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)(kGbFloats * sizeof(float)));
+    if (e != cudaSuccess) return e;
+    configured_device.store(dev);
+  }
+  LaunchScope ls(kKRasterBwdGw, s);
+  return launch_chain(k_raster_bwd_gblock, dim3((unsigned)w.n_gblocks), dim3(kGbWarps * 32),
+                      kGbFloats * sizeof(float), s, w);
+}
 
 cudaError_t launch_raster_bwd_gw(const Ws& w, cudaStream_t s) {
   if (w.n == 0) return cudaSuccess;

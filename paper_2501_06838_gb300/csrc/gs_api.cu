@@ -310,6 +310,14 @@ gs_status prepare(int32_t n_images, const gs_gaussians* g, const gs_view* v, voi
   w.n_pairs = (int32_t)pairs;
   w.pair = c->P.pair;
   w.adjoint = c->P.adjoint;
+  // 8 x 8 blocks of LR cells (the Gaussian-warp adjoint's block form), when
+  // every image's Gaussians sit on a reference grid
+  int64_t gblocks = 0;
+  for (int i = 0; i < n_images; ++i) {
+    if (g[i].ref_grid_m == 0) { gblocks = 0; break; }
+    gblocks += (int64_t)((v[i].lr_h + 7) / 8) * ((v[i].lr_w + 7) / 8);
+  }
+  w.n_gblocks = gblocks < (1LL << 31) ? (int32_t)gblocks : 0;
   return GS_OK;
 }
 
@@ -317,7 +325,7 @@ gs_status upload_images(const Call& c, const gs_gaussians* g, const gs_view* v, 
                         const float* const* grad_outs, float* const* grads, int reset,
                         cudaStream_t s) {
   int64_t gbase = 0;
-  int tbase = 0, pbase = 0;
+  int tbase = 0, pbase = 0, bbase = 0;
   const int tile = c.P.tile;
   for (int first = 0; first < c.P.n_images; first += kSetupChunk) {
     SetupChunk ch;
@@ -363,7 +371,9 @@ gs_status upload_images(const Call& c, const gs_gaussians* g, const gs_view* v, 
       d.tiles_y = (v[i].out_h + tile - 1) / tile;
       d.t_base = tbase;
       d.p_base = pbase;
+      d.b_base = bbase;
       gbase += g[i].n;
+      bbase += ((v[i].lr_h + 7) / 8) * ((v[i].lr_w + 7) / 8);
       tbase += d.tiles_x * d.tiles_y;
       pbase += d.tiles_y * ((d.tiles_x + 1) / 2);
     }
@@ -444,7 +454,9 @@ gs_status run_backward(int32_t n_images, const gs_gaussians* g, const gs_view* v
     if (e != cudaSuccess) return cuda_fail(e, "raster_bwd");
   } else {
     // one warp per Gaussian writes all its moments: no clearing, no atomics
-    e = launch_raster_bwd_gw(c.w, s);
+    // (blocks of LR cells staging the gradient in shared memory when the
+    // Gaussians sit on a reference grid)
+    e = c.w.n_gblocks > 0 ? launch_raster_bwd_gblock(c.w, s) : launch_raster_bwd_gw(c.w, s);
     if (e != cudaSuccess) return cuda_fail(e, "raster_bwd_gw");
   }
   e = launch_preprocess_bwd(c.w, s);

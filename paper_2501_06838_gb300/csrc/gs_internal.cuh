@@ -37,7 +37,8 @@ struct ImageDesc {
   float h_sigma_lo, h_sigma_span, h_rho_scale, h_offset_scale;
   int32_t row0;   // first image row of the output (a band; 0: the whole image)
   int32_t p_base; // grid binning, tile 16: first global index of this image's tile pairs
-  int32_t pad_[2];
+  int32_t b_base; // m > 0: first global index of this image's 8 x 8 blocks of LR cells
+  int32_t pad_;
 };
 // ImageDesc::flags
 constexpr int32_t kFlagPeak = 1;   // Z = 1 instead of Eq. 2's normalisation
@@ -109,7 +110,7 @@ struct Ws {
   int32_t n_pairs;            // grid binning, tile 16: horizontal tile pairs over all images
   int32_t pair;               // 1: the forward raster runs one warp per pair of tiles
   int32_t adjoint;            // the adjoint kernel of these views (gs_adjoint, resolved)
-  int32_t pad_;
+  int32_t n_gblocks;          // every image with m > 0: 8 x 8 blocks of LR cells in all; else 0
   const float* grad_out0;     // direct: dL/dI of image 0
   float* grads0;              // direct: parameter gradients of image 0
 };
@@ -227,6 +228,7 @@ cudaError_t launch_sort(const Ws& w, int key_bits, cudaStream_t s, int* final_bu
 cudaError_t launch_ranges(const Ws& w, const uint32_t* sorted_keys, cudaStream_t s);
 cudaError_t launch_raster_fwd(const Ws& w, const uint32_t* sorted_vals, int batch, cudaStream_t s);
 cudaError_t launch_raster_bwd_gw(const Ws& w, cudaStream_t s);
+cudaError_t launch_raster_bwd_gblock(const Ws& w, cudaStream_t s);   // needs w.n_gblocks > 0
 // quadrants: walk the 8 x 8 quadrants of 16 x 16 tiles (tile 16 only), each
 // with the Gaussians of the tile's list whose window meets it
 cudaError_t launch_raster_bwd_tile(const Ws& w, const uint32_t* lists, bool quadrants,
