@@ -25,6 +25,7 @@
 // so d stays finite, e = -1e36 and w = +0 with no branch.
 #include <atomic>
 #include <climits>
+#include <type_traits>
 
 #include "gs_internal.cuh"
 
@@ -71,11 +72,11 @@ struct GwAcc {
 // element offset `off` (second column at `off2` when the row is not 8-byte
 // aligned).
 // SMEM: the three planes are a staged copy in shared memory (always aligned).
-template <bool ALIGNED, bool SMEM>
+template <bool ALIGNED, bool SMEM, typename Off>
 __device__ __forceinline__ void gw_pixel_pair(GwAcc& a, const float* __restrict__ g0,
                                               const float* __restrict__ g1,
-                                              const float* __restrict__ g2, int64_t off,
-                                              int64_t off2, const float4 q, float2 Xs, float2 nsK,
+                                              const float* __restrict__ g2, Off off,
+                                              Off off2, const float4 q, float2 Xs, float2 nsK,
                                               float2 cr, float2 cg, float2 cb) {
   float2 gr, gg, gb;
   if (SMEM) {
@@ -118,6 +119,7 @@ __device__ __forceinline__ void gw_walk(const float* __restrict__ go, int64_t pl
                                         int oy, int x0, int x1, int y0, int y1, const float4 f0,
                                         const float4 f1, const float4 f2, float4* rt, int lane,
                                         float (&v)[8]) {
+  using Off = typename std::conditional<SMEM, int, int64_t>::type;
   const float cxh = f0.x, cxl = f0.y, cyh = f0.z, cyl = f0.w;
   const float sA = f1.x, gq = f1.z, l = f1.w;
   const float2 nsK = p2(-f1.y, -f1.y);
@@ -156,13 +158,14 @@ __device__ __forceinline__ void gw_walk(const float* __restrict__ go, int64_t pl
       a.C[0] = a.C[1] = a.C[2] = a.SY = a.SYY = a.Sd = a.Sdd = a.SdY = p2(0.f, 0.f);
       int r = lr;
       for (; r + rpi < nr; r += 2 * rpi) {
-        const int64_t ya = (int64_t)(rb + r - oy) * W, yb = ya + (int64_t)rpi * W;
+        // 32-bit offsets within a staged region, 64-bit within an image
+        const Off ya = (Off)(rb + r - oy) * W, yb = ya + (Off)rpi * W;
         const float4 qa = rt[r], qb = rt[r + rpi];
         gw_pixel_pair<ALIGNED, SMEM>(a, g0, g1, g2, ya + xl, ya + xq, qa, Xs, nsK, cr, cg, cb);
         gw_pixel_pair<ALIGNED, SMEM>(a, g0, g1, g2, yb + xl, yb + xq, qb, Xs, nsK, cr, cg, cb);
       }
       if (r < nr) {
-        const int64_t ya = (int64_t)(rb + r - oy) * W;
+        const Off ya = (Off)(rb + r - oy) * W;
         gw_pixel_pair<ALIGNED, SMEM>(a, g0, g1, g2, ya + xl, ya + xq, rt[r], Xs, nsK, cr, cg, cb);
       }
       tSd = __fadd2_rn(tSd, a.Sd);
@@ -243,6 +246,7 @@ __global__ void __launch_bounds__(kGbWarps * 32) k_raster_bwd_gblock(Ws w) {
   extern __shared__ float2 gstage2[];   // [3][RH][RW] floats (float2 for the alignment)
   float* gstage = reinterpret_cast<float*>(gstage2);
   __shared__ float4 rt[kGbWarps][kGwRows];
+  __shared__ float4 srec[kGbCells * kGbCells * kRecordF4];   // the records when m = 1
   __shared__ int sbox[4];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int im = image_of_gblock(w.images, w.n_images, (int)blockIdx.x);
@@ -269,7 +273,14 @@ __global__ void __launch_bounds__(kGbWarps * 32) k_raster_bwd_gblock(Ws w) {
   {
     int bx0 = INT_MAX, bx1 = INT_MIN, by0 = INT_MAX, by1 = INT_MIN;
     for (int k = threadIdx.x; k < ng; k += blockDim.x) {
-      const float4 f3 = w.records[gid_of(k) * kRecordF4 + 3];
+      const float4* rec = w.records + gid_of(k) * kRecordF4;
+      const float4 f3 = rec[3];
+      if (m == 1) {   // ng <= 64: the warps read the records from shared memory
+        srec[k * kRecordF4] = rec[0];
+        srec[k * kRecordF4 + 1] = rec[1];
+        srec[k * kRecordF4 + 2] = rec[2];
+        srec[k * kRecordF4 + 3] = f3;
+      }
       const int x0 = __float_as_int(f3.x), x1 = __float_as_int(f3.y);
       const int y0 = __float_as_int(f3.z), y1 = __float_as_int(f3.w);
       if (x0 <= x1 && y0 <= y1) {
@@ -309,7 +320,7 @@ __global__ void __launch_bounds__(kGbWarps * 32) k_raster_bwd_gblock(Ws w) {
   const bool aligned = (W & 1) == 0 && (reinterpret_cast<uintptr_t>(go) & 7) == 0;
   for (int k = wp; k < ng; k += kGbWarps) {
     const int64_t gi = gid_of(k);
-    const float4* rec = w.records + gi * kRecordF4;
+    const float4* rec = m == 1 ? srec + k * kRecordF4 : w.records + gi * kRecordF4;
     const float4 f3 = rec[3];
     const int x0 = __float_as_int(f3.x), x1 = __float_as_int(f3.y);
     const int y0 = __float_as_int(f3.z), y1 = __float_as_int(f3.w);
