@@ -218,6 +218,21 @@ __global__ void __launch_bounds__(kGwWarps * 32) k_raster_bwd_gw(Ws w) {
   if ((lane & 3) == 0) w.grec[gi * 12 + (lane >> 2)] = s;
 }
 
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, int src_bytes) {
+  // 4-byte asynchronous copy; bytes past src_bytes (0 or 4) are filled with zeros
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void cp_async16z(void* smem, const void* gmem, int src_bytes) {
+  // 16-byte asynchronous copy; bytes past src_bytes (0 or 16) are filled with zeros
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem),
+               "r"(src_bytes)
+               : "memory");
+}
+
 // Block form, for Gaussians on a reference grid (m > 0): one CTA per block of
 // kGbCells x kGbCells LR cells of an image. The CTA first forms the union box
 // of its Gaussians' windows and, when the box fits kGbFloats, copies the
@@ -243,8 +258,8 @@ __device__ __forceinline__ int image_of_gblock(const ImageDesc* im, int n_images
 __global__ void __launch_bounds__(kGbWarps * 32) k_raster_bwd_gblock(Ws w) {
   griddep_release();
   griddep_wait();
-  extern __shared__ float2 gstage2[];   // [3][RH][RW] floats (float2 for the alignment)
-  float* gstage = reinterpret_cast<float*>(gstage2);
+  extern __shared__ float4 gstage4[];   // [3][RH][RW] floats (float4 for 16-byte alignment)
+  float* gstage = reinterpret_cast<float*>(gstage4);
   __shared__ float4 rt[kGbWarps][kGwRows];
   __shared__ float4 srec[kGbCells * kGbCells * kRecordF4];   // the records when m = 1
   __shared__ int sbox[4];
@@ -297,24 +312,52 @@ __global__ void __launch_bounds__(kGbWarps * 32) k_raster_bwd_gblock(Ws w) {
     }
   }
   __syncthreads();
-  const int rx0 = sbox[0] & ~1, rx1 = sbox[1], ry0 = sbox[2], ry1 = sbox[3];
+  const int W = D.out_w;
+  const float* go = w.direct ? w.grad_out0 : D.grad_out;
+  // 16-byte copies when the output's rows allow them: the box then starts on
+  // a multiple of 4 columns and spans a multiple of 4 (else of 2)
+  const bool vec4 = (W & 3) == 0 && (reinterpret_cast<uintptr_t>(go) & 15) == 0;
+  const int al = vec4 ? 3 : 1;
+  const int rx0 = sbox[0] & ~al, rx1 = sbox[1], ry0 = sbox[2], ry1 = sbox[3];
   const bool any = rx0 <= rx1 && ry0 <= ry1;
-  const int RW = any ? ((rx1 - rx0 + 2) & ~1) : 0, RH = any ? ry1 - ry0 + 1 : 0;
+  const int RW = any ? ((rx1 - rx0 + 1 + al) & ~al) : 0, RH = any ? ry1 - ry0 + 1 : 0;
   const int64_t rplane = (int64_t)RW * RH;
   const bool staged = any && 3 * rplane <= kGbFloats;   // uniform over the CTA
-  const int W = D.out_w;
   const int64_t plane = (int64_t)D.out_h * W;
-  const float* go = w.direct ? w.grad_out0 : D.grad_out;
-  if (staged) {
-    for (int64_t idx = threadIdx.x; idx < rplane; idx += blockDim.x) {
-      const int r = (int)(idx / RW), x = (int)(idx - (int64_t)r * RW);
-      const int gx = rx0 + x, gy = ry0 + r - D.row0;   // output row
-      const bool in = gx < W;                            // rows are inside the output
-      const int64_t o = in ? (int64_t)gy * W + gx : 0;
-      gstage[idx] = in ? __ldg(go + o) : 0.0f;
-      gstage[rplane + idx] = in ? __ldg(go + plane + o) : 0.0f;
-      gstage[2 * rplane + idx] = in ? __ldg(go + 2 * plane + o) : 0.0f;
+  if (staged && vec4) {
+    const int RW4 = RW >> 2;
+    for (int r = wp; r < RH; r += kGbWarps) {
+      const float* src = go + (int64_t)(ry0 + r - D.row0) * W;   // output row (inside the output)
+      float* dst = gstage + r * RW;
+      for (int x4 = lane; x4 < RW4; x4 += 32) {
+        const int gx = rx0 + 4 * x4;
+        const bool in = gx < W;      // all four columns or none (W a multiple of 4)
+        const int o = in ? gx : 0;   // always a valid address
+        const int nb = in ? 16 : 0;
+        cp_async16z(dst + 4 * x4, src + o, nb);
+        cp_async16z(dst + rplane + 4 * x4, src + plane + o, nb);
+        cp_async16z(dst + 2 * rplane + 4 * x4, src + 2 * plane + o, nb);
+      }
     }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+  } else if (staged) {
+    // one warp per row of the box, its lanes along the row (coalesced), as
+    // asynchronous copies so that all of a thread's loads are in flight at once
+    // (columns past the output's edge are filled with zeros)
+    for (int r = wp; r < RH; r += kGbWarps) {
+      const float* src = go + (int64_t)(ry0 + r - D.row0) * W;   // output row (inside the output)
+      float* dst = gstage + r * RW;
+      for (int x = lane; x < RW; x += 32) {
+        const int gx = rx0 + x;
+        const bool in = gx < W;
+        const int o = in ? gx : 0;   // always a valid address
+        const int nb = in ? 4 : 0;
+        cp_async4(dst + x, src + o, nb);
+        cp_async4(dst + rplane + x, src + plane + o, nb);
+        cp_async4(dst + 2 * rplane + x, src + 2 * plane + o, nb);
+      }
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
   }
   __syncthreads();
   const bool aligned = (W & 1) == 0 && (reinterpret_cast<uintptr_t>(go) & 7) == 0;
