@@ -234,7 +234,7 @@ __device__ __forceinline__ void cp_async16z(void* smem, const void* gmem, int sr
 }
 
 // Block form, for Gaussians on a reference grid (m > 0): one CTA per block of
-// kGbCells x kGbCells LR cells of an image. The CTA first forms the union box
+// kGbCellsX x kGbCellsY LR cells of an image. The CTA first forms the union box
 // of its Gaussians' windows and, when the box fits kGbFloats, copies the
 // upstream gradient over it into shared memory once (three planes, the first
 // column even and the width even); its warps then walk their Gaussians (the
@@ -242,7 +242,6 @@ __device__ __forceinline__ void cp_async16z(void* smem, const void* gmem, int sr
 // does, reading the gradient from shared memory instead of L1/L2. A block
 // whose box does not fit walks the gradient in global memory. Each Gaussian's
 // sums keep the one-warp form's order, so the moments are the same bits.
-constexpr int kGbCells = 8;
 constexpr int kGbWarps = 8;
 constexpr int kGbFloats = 24 * 1024;   // 96 KB of staged gradient at most
 
@@ -261,16 +260,16 @@ __global__ void __launch_bounds__(kGbWarps * 32) k_raster_bwd_gblock(Ws w) {
   extern __shared__ float4 gstage4[];   // [3][RH][RW] floats (float4 for 16-byte alignment)
   float* gstage = reinterpret_cast<float*>(gstage4);
   __shared__ float4 rt[kGbWarps][kGwRows];
-  __shared__ float4 srec[kGbCells * kGbCells * kRecordF4];   // the records when m = 1
+  __shared__ float4 srec[kGbCellsX * kGbCellsY * kRecordF4];   // the records when m = 1
   __shared__ int sbox[4];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int im = image_of_gblock(w.images, w.n_images, (int)blockIdx.x);
   const ImageDesc& D = w.images[im];
-  const int bxs = (D.lr_w + kGbCells - 1) / kGbCells;
+  const int bxs = (D.lr_w + kGbCellsX - 1) / kGbCellsX;
   const int lb = (int)blockIdx.x - D.b_base;
   const int by = lb / bxs, bx = lb - by * bxs;
-  const int j0 = bx * kGbCells, i0 = by * kGbCells;
-  const int cw = min(kGbCells, D.lr_w - j0), ch = min(kGbCells, D.lr_h - i0);
+  const int j0 = bx * kGbCellsX, i0 = by * kGbCellsY;
+  const int cw = min(kGbCellsX, D.lr_w - j0), ch = min(kGbCellsY, D.lr_h - i0);
   const int m = D.m;
   const int ng = cw * ch * m;
   // global id of the block's k-th Gaussian (cells row by row, m per cell)
@@ -290,7 +289,7 @@ __global__ void __launch_bounds__(kGbWarps * 32) k_raster_bwd_gblock(Ws w) {
     for (int k = threadIdx.x; k < ng; k += blockDim.x) {
       const float4* rec = w.records + gid_of(k) * kRecordF4;
       const float4 f3 = rec[3];
-      if (m == 1) {   // ng <= 64: the warps read the records from shared memory
+      if (m == 1) {   // one Gaussian per cell: the warps read the records from shared memory
         srec[k * kRecordF4] = rec[0];
         srec[k * kRecordF4 + 1] = rec[1];
         srec[k * kRecordF4 + 2] = rec[2];

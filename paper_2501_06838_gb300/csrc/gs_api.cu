@@ -310,12 +310,13 @@ gs_status prepare(int32_t n_images, const gs_gaussians* g, const gs_view* v, voi
   w.n_pairs = (int32_t)pairs;
   w.pair = c->P.pair;
   w.adjoint = c->P.adjoint;
-  // 8 x 8 blocks of LR cells (the Gaussian-warp adjoint's block form), when
+  // blocks of LR cells (the Gaussian-warp adjoint's block form), when
   // every image's Gaussians sit on a reference grid
   int64_t gblocks = 0;
   for (int i = 0; i < n_images; ++i) {
     if (g[i].ref_grid_m == 0) { gblocks = 0; break; }
-    gblocks += (int64_t)((v[i].lr_h + 7) / 8) * ((v[i].lr_w + 7) / 8);
+    gblocks += (int64_t)((v[i].lr_h + kGbCellsY - 1) / kGbCellsY) *
+               ((v[i].lr_w + kGbCellsX - 1) / kGbCellsX);
   }
   w.n_gblocks = gblocks < (1LL << 31) ? (int32_t)gblocks : 0;
   return GS_OK;
@@ -373,7 +374,7 @@ gs_status upload_images(const Call& c, const gs_gaussians* g, const gs_view* v, 
       d.p_base = pbase;
       d.b_base = bbase;
       gbase += g[i].n;
-      bbase += ((v[i].lr_h + 7) / 8) * ((v[i].lr_w + 7) / 8);
+      bbase += ((v[i].lr_h + kGbCellsY - 1) / kGbCellsY) * ((v[i].lr_w + kGbCellsX - 1) / kGbCellsX);
       tbase += d.tiles_x * d.tiles_y;
       pbase += d.tiles_y * ((d.tiles_x + 1) / 2);
     }

@@ -15,6 +15,8 @@ enum : uint32_t { kStInvalid = 1u, kStCapacity = 2u, kStInternal = 4u, kStTimeou
 constexpr int kSetupChunk = 16;       // image descriptors per setup launch
 constexpr int kFootprintBlock = 256;  // Gaussians per footprint / emit block
 constexpr int kRecordF4 = 4;          // a record is 4 float4 = 64 B
+constexpr int kGbCellsX = 8;          // LR cells per block of the block Gaussian-warp adjoint
+constexpr int kGbCellsY = 8;
 
 // Per-image descriptor, copied into the workspace at the start of each call.
 struct ImageDesc {
@@ -37,7 +39,7 @@ struct ImageDesc {
   float h_sigma_lo, h_sigma_span, h_rho_scale, h_offset_scale;
   int32_t row0;   // first image row of the output (a band; 0: the whole image)
   int32_t p_base; // grid binning, tile 16: first global index of this image's tile pairs
-  int32_t b_base; // m > 0: first global index of this image's 8 x 8 blocks of LR cells
+  int32_t b_base; // m > 0: first global index of this image's blocks of LR cells
   int32_t pad_;
 };
 // ImageDesc::flags
@@ -110,7 +112,7 @@ struct Ws {
   int32_t n_pairs;            // grid binning, tile 16: horizontal tile pairs over all images
   int32_t pair;               // 1: the forward raster runs one warp per pair of tiles
   int32_t adjoint;            // the adjoint kernel of these views (gs_adjoint, resolved)
-  int32_t n_gblocks;          // every image with m > 0: 8 x 8 blocks of LR cells in all; else 0
+  int32_t n_gblocks;          // every image with m > 0: blocks of LR cells in all; else 0
   const float* grad_out0;     // direct: dL/dI of image 0
   float* grads0;              // direct: parameter gradients of image 0
 };
