@@ -98,7 +98,10 @@ typedef enum { GS_ALIGN_EQ4 = 0, GS_ALIGN_HALF = 1 } gs_align;
  *             every lane at once); each (tile, Gaussian) sum is added with
  *             atomics (summation order varies run to run);
  *   GAUSSIAN: one warp per Gaussian over its own window, one fixed summation
- *             order, no atomics: bitwise deterministic;
+ *             order, no atomics: bitwise deterministic (when every image has
+ *             ref_grid_m > 0 the warps work in CTAs over 8 x 8 blocks of LR
+ *             cells, with the upstream gradient under the block staged in
+ *             shared memory; the sums are the same);
  *   QUADRANT: TILE over the 8 x 8 quadrants of 16 x 16 tiles: each quadrant's
  *             warp keeps, from the tile's list, the Gaussians whose window
  *             meets the quadrant, so small windows waste fewer pixel
