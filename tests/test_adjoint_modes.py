@@ -149,3 +149,35 @@ def test_quadrant_long_lists_partial_hits():
     _, ws = gs.render(device_gaussians(g), v, check=True)
     st = gs.read_stats(ws)
     assert st["adjoint"] == QUADRANT and st["tile_pairs"] > 64 * st["n_tiles"]
+
+
+def test_gaussian_mode_blocks_mixed_grids_and_partial_blocks():
+    """The Gaussian-warp adjoint in blocks of 8 x 8 LR cells: one batch with
+    m = 1, 4 and 9 images whose LR sizes are not multiples of 8 (partial
+    blocks at the right and bottom edges), output widths with and without
+    16-byte rows; and a batch with an absolute-centre image (m = 0), which
+    runs the one-warp-per-Gaussian launch for every image."""
+    import torch
+    import paper_2501_06838_gb300 as gs
+    for ms in ((1, 4, 9), (1, 0)):
+        gsets, views = [], []
+        for i, m in enumerate(ms):
+            h, w, s = 13 + 5 * i, 19 + 3 * i, 3.25 - 0.5 * i
+            if m == 0:
+                rng = np.random.default_rng(80 + i)
+                n = h * w
+                mu = np.stack([rng.uniform(0, w, n), rng.uniform(0, h, n)], 1)
+                gsets.append(absolute(mu, rng.uniform(0.2, 2.0, (n, 2)), rng.uniform(-0.9, 0.9, n),
+                                      rng.uniform(0, 1, (n, 3)), rng.uniform(0, 1, n), h, w))
+            else:
+                gsets.append(S.draw_gaussians(80 + i, h, w, m, (0.2, 2.0)))
+            v = S.View(h, w, S.out_size(h, s), S.out_size(w, s), s)
+            v.adjoint = GAUSSIAN
+            views.append(v)
+        dgs = [device_gaussians(g) for g in gsets]
+        _, ws = gs.render_batched(dgs, views, check=True)
+        gos = [S.grad_out(90 + i, v.out_h, v.out_w) for i, v in enumerate(views)]
+        grads = gs.render_batched_bwd(dgs, views, [torch.from_numpy(x.astype(np.float32)).cuda()
+                                                   for x in gos], ws, check=True)
+        for g, v, go, gr in zip(gsets, views, gos, grads):
+            _check(gr.cpu().double().numpy(), oracle.adjoint(g, v, go))
